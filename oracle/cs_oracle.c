@@ -1,0 +1,383 @@
+/*
+ * cs_oracle.c -- plain FP64 CPU oracle for the regularised smooth-contact solve
+ * and its implicit-function-theorem adjoint.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA path; the two meet only in the seeded
+ * input generators.
+ *
+ * What it computes (per instance, Section III of the paper):
+ *   a0   = M^-1 qfrc                                  (Eq. 1, qfrc = tau - c)
+ *   L(a) = 1/2 (a-a0)^T M (a-a0) + 1/2 sum_i D_i min(jar_i,0)^2,
+ *          jar = J a - aref                           (Eq. 5, pyramidal rows,
+ *                                                      D = R^-1 of Eq. 4)
+ *   r(a) = M a - qfrc + J^T f,  f = D . min(jar,0)    (Eqs. 6 and 8)
+ *   H(a) = M + J^T diag(D . [jar<0]) J                (Eq. 9)
+ *   Newton: p = -H^-1 r, a <- a + alpha p             (Eq. 10), alpha from an
+ *   exact search of the convex piecewise-quadratic phi(alpha) = L(a+alpha p).
+ *   Adjoint at the returned a (Eq. 17 with F_a = H symmetric):
+ *     H w = g;  dL/dqfrc = w;  dL/daref = D_act . (J w);
+ *     dL/dJ = -(f w^T + (D_act . J w) a^T).
+ *
+ * Everything is written out plainly in double precision: dense unblocked
+ * Cholesky, explicit loops, qsort for the line-search breakpoints.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum {
+  OR_OK = 0,          /* ||r||_inf <= tol * scale, or exact termination */
+  OR_MAXITER = 1,     /* Newton step cap reached */
+  OR_CHOLFAIL = 2,    /* non-positive pivot */
+  OR_NONFINITE = 3,   /* NaN/Inf met */
+  OR_BADSHAPE = 4,    /* nv < 1 or m < 0 */
+  OR_NOPROGRESS = 5   /* p^T r >= 0: no descent direction */
+};
+
+/* ---- dense helpers ------------------------------------------------------ */
+
+/* In-place Cholesky of the n x n row-major SPD matrix A (lower triangle used
+ * and overwritten by L, upper triangle zeroed).  Returns 0, or -1 on a
+ * non-positive pivot. */
+static int chol(int n, double *A) {
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * n + j];
+    for (int k = 0; k < j; ++k) d -= A[j * n + k] * A[j * n + k];
+    if (!(d > 0.0)) return -1;
+    double ljj = sqrt(d);
+    A[j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double s = A[i * n + j];
+      for (int k = 0; k < j; ++k) s -= A[i * n + k] * A[j * n + k];
+      A[i * n + j] = s / ljj;
+    }
+    for (int k = j + 1; k < n; ++k) A[j * n + k] = 0.0;
+  }
+  return 0;
+}
+
+/* x <- (L L^T)^-1 x. */
+static void chol_solve(int n, const double *L, double *x) {
+  for (int i = 0; i < n; ++i) {
+    double s = x[i];
+    for (int k = 0; k < i; ++k) s -= L[i * n + k] * x[k];
+    x[i] = s / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = x[i];
+    for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+    x[i] = s / L[i * n + i];
+  }
+}
+
+static double inf_norm(int n, const double *x) {
+  double v = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double a = fabs(x[i]);
+    if (a > v || a != a) v = a;
+  }
+  return v;
+}
+
+/* ---- problem pieces ----------------------------------------------------- */
+
+typedef struct {
+  int nv, m;
+  const double *M, *J, *qfrc, *aref, *D;
+} problem;
+
+/* jar = J a - aref, act = [jar < 0], f = D . min(jar, 0),
+ * Ma = M a, Jtf = J^T f, r = Ma - qfrc + Jtf (Eqs. 6 and 8).
+ * Returns the scale max(1, |qfrc|, |Ma|, |Jtf|) used by the stopping test. */
+static double residual(const problem *P, const double *a, double *jar,
+                       uint8_t *act, double *f, double *Ma, double *Jtf,
+                       double *r) {
+  const int nv = P->nv, m = P->m;
+  for (int i = 0; i < m; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < nv; ++k) s += P->J[i * nv + k] * a[k];
+    jar[i] = s - P->aref[i];
+    act[i] = jar[i] < 0.0;
+    f[i] = act[i] ? P->D[i] * jar[i] : 0.0;
+  }
+  for (int j = 0; j < nv; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < nv; ++k) s += P->M[j * nv + k] * a[k];
+    Ma[j] = s;
+    double t = 0.0;
+    for (int i = 0; i < m; ++i) t += P->J[i * nv + j] * f[i];
+    Jtf[j] = t;
+    r[j] = Ma[j] - P->qfrc[j] + Jtf[j];
+  }
+  double scale = 1.0, v;
+  if ((v = inf_norm(nv, P->qfrc)) > scale) scale = v;
+  if ((v = inf_norm(nv, Ma)) > scale) scale = v;
+  if ((v = inf_norm(nv, Jtf)) > scale) scale = v;
+  return scale;
+}
+
+/* H = M + sum_{i active} D_i J_i^T J_i (Eq. 9), full symmetric. */
+static void newton_matrix(const problem *P, const uint8_t *act, double *H) {
+  const int nv = P->nv, m = P->m;
+  memcpy(H, P->M, sizeof(double) * nv * nv);
+  for (int i = 0; i < m; ++i) {
+    if (!act[i]) continue;
+    const double *Ji = P->J + (size_t)i * nv;
+    for (int j = 0; j < nv; ++j)
+      for (int k = 0; k < nv; ++k) H[j * nv + k] += P->D[i] * Ji[j] * Ji[k];
+  }
+}
+
+typedef struct {
+  double alpha;
+  int row;
+} breakpoint;
+
+static int bp_cmp(const void *x, const void *y) {
+  double a = ((const breakpoint *)x)->alpha, b = ((const breakpoint *)y)->alpha;
+  return (a > b) - (a < b);
+}
+
+/* Exact minimiser of phi(alpha) = L(a + alpha p) over alpha > 0.
+ *
+ * phi'(alpha) = p^T (M (a + alpha p) - qfrc) + sum_i D_i s_i min(jar_i + alpha s_i, 0)
+ * with s = J p.  phi' is continuous, piecewise linear and increasing (phi is
+ * strongly convex along p because p^T M p > 0).  On each interval between
+ * breakpoints alpha_i = -jar_i / s_i it equals c0 + c1 alpha, where the sums
+ * run over the rows active on that interval.  The breakpoints are sorted and
+ * swept in increasing order; the first interval that contains the root of
+ * its line returns it. */
+static double line_search(const problem *P, const double *a, const double *p,
+                          const double *jar, const double *Ma, double *s,
+                          breakpoint *bp) {
+  const int nv = P->nv, m = P->m;
+  double c0 = 0.0, c1 = 0.0;
+  for (int j = 0; j < nv; ++j) {
+    double Mp = 0.0;
+    for (int k = 0; k < nv; ++k) Mp += P->M[j * nv + k] * p[k];
+    c0 += p[j] * (Ma[j] - P->qfrc[j]);
+    c1 += p[j] * Mp;
+  }
+  int nb = 0;
+  for (int i = 0; i < m; ++i) {
+    double si = 0.0;
+    for (int k = 0; k < nv; ++k) si += P->J[i * nv + k] * p[k];
+    s[i] = si;
+    /* active just to the right of alpha = 0 */
+    int on = jar[i] < 0.0 || (jar[i] == 0.0 && si < 0.0);
+    if (on) {
+      c0 += P->D[i] * si * jar[i];
+      c1 += P->D[i] * si * si;
+    }
+    if (si != 0.0) {
+      double al = -jar[i] / si;
+      if (al > 0.0) {
+        bp[nb].alpha = al;
+        bp[nb].row = i;
+        ++nb;
+      }
+    }
+  }
+  qsort(bp, nb, sizeof(breakpoint), bp_cmp);
+  for (int q = 0; q < nb; ++q) {
+    double root = -c0 / c1;
+    if (root <= bp[q].alpha) return root;
+    /* cross the breakpoint: row toggles */
+    int i = bp[q].row;
+    double sgn = (jar[i] < 0.0) ? -1.0 : 1.0; /* leaves if it was active */
+    c0 += sgn * P->D[i] * s[i] * jar[i];
+    c1 += sgn * P->D[i] * s[i] * s[i];
+  }
+  return -c0 / c1;
+}
+
+/* ---- public entry points ------------------------------------------------ */
+
+/* Solve one instance.  a (out, nv) holds the returned acceleration; act (out,
+ * m) its active set; *iters the Newton steps taken.  a_init may be NULL
+ * (start at a0 = M^-1 qfrc) or a warm start.  Returns a status code. */
+int oracle_solve(int nv, int m, const double *M, const double *J,
+                 const double *qfrc, const double *aref, const double *D,
+                 const double *a_init, double tol, int max_iter, double *a,
+                 uint8_t *act, int *iters) {
+  *iters = 0;
+  if (nv < 1 || m < 0) return OR_BADSHAPE;
+  problem P = {nv, m, M, J, qfrc, aref, D};
+  size_t wd = (size_t)(6 * m + 6 * nv + 2 * nv * nv + 8);
+  double *w = (double *)calloc(wd, sizeof(double));
+  breakpoint *bp = (breakpoint *)calloc((size_t)m + 1, sizeof(breakpoint));
+  uint8_t *act2 = (uint8_t *)calloc((size_t)m + 1, 1);
+  double *jar = w, *f = jar + m, *s = f + m, *jar2 = s + m, *Ma = jar2 + m;
+  double *Jtf = Ma + nv, *r = Jtf + nv, *p = r + nv, *an = p + nv;
+  double *H = an + nv;
+  int status = OR_MAXITER;
+
+  if (a_init) {
+    memcpy(a, a_init, sizeof(double) * nv);
+  } else { /* a0 = M^-1 qfrc (Eq. 1) */
+    memcpy(H, M, sizeof(double) * nv * nv);
+    if (chol(nv, H)) { status = OR_CHOLFAIL; goto done; }
+    memcpy(a, qfrc, sizeof(double) * nv);
+    chol_solve(nv, H, a);
+  }
+
+  for (int k = 0;; ++k) {
+    double scale = residual(&P, a, jar, act, f, Ma, Jtf, r);
+    double rn = inf_norm(nv, r);
+    if (!isfinite(rn) || !isfinite(scale)) { status = OR_NONFINITE; break; }
+    if (rn <= tol * scale) { status = OR_OK; break; }
+    if (k >= max_iter) { status = OR_MAXITER; break; }
+    newton_matrix(&P, act, H);
+    if (chol(nv, H)) { status = OR_CHOLFAIL; break; }
+    for (int j = 0; j < nv; ++j) p[j] = -r[j];
+    chol_solve(nv, H, p);
+    double ptr = 0.0;
+    for (int j = 0; j < nv; ++j) ptr += p[j] * r[j];
+    if (!(ptr < 0.0)) { status = OR_NOPROGRESS; break; }
+    /* Exact termination: if the full step keeps the active set, a + p is the
+     * minimiser of the quadratic on that set and consistent with it, hence
+     * the exact solution. */
+    for (int j = 0; j < nv; ++j) an[j] = a[j] + p[j];
+    int same = 1;
+    for (int i = 0; i < m; ++i) {
+      double v = 0.0;
+      for (int q = 0; q < nv; ++q) v += J[i * nv + q] * an[q];
+      jar2[i] = v - aref[i];
+      act2[i] = jar2[i] < 0.0;
+      if (act2[i] != act[i]) same = 0;
+    }
+    if (same) {
+      memcpy(a, an, sizeof(double) * nv);
+      *iters = k + 1;
+      residual(&P, a, jar, act, f, Ma, Jtf, r);
+      status = OR_OK;
+      break;
+    }
+    double alpha = line_search(&P, a, p, jar, Ma, s, bp);
+    for (int j = 0; j < nv; ++j) a[j] += alpha * p[j];
+    *iters = k + 1;
+  }
+done:
+  free(w);
+  free(bp);
+  free(act2);
+  return status;
+}
+
+/* Adjoint at the returned a (Eq. 17): H(a) w = g with the active set of a,
+ * then dqfrc = w, daref = D_act . (J w), dJ = -(f w^T + daref a^T).
+ * act (out, m) receives the active set used.  Returns 0 or OR_CHOLFAIL. */
+int oracle_adjoint(int nv, int m, const double *M, const double *J,
+                   const double *qfrc, const double *aref, const double *D,
+                   const double *a, const double *g, double *dqfrc,
+                   double *daref, double *dJ, uint8_t *act) {
+  if (nv < 1 || m < 0) return OR_BADSHAPE;
+  problem P = {nv, m, M, J, qfrc, aref, D};
+  double *w = (double *)calloc((size_t)(3 * m + 3 * nv + nv * nv + 8), sizeof(double));
+  double *jar = w, *f = jar + m, *u = f + m, *Ma = u + m, *Jtf = Ma + nv;
+  double *r = Jtf + nv, *H = r + nv;
+  int status = 0;
+  residual(&P, a, jar, act, f, Ma, Jtf, r);
+  newton_matrix(&P, act, H);
+  if (chol(nv, H)) { status = OR_CHOLFAIL; goto done; }
+  memcpy(dqfrc, g, sizeof(double) * nv);
+  chol_solve(nv, H, dqfrc);
+  for (int i = 0; i < m; ++i) {
+    double v = 0.0;
+    for (int k = 0; k < nv; ++k) v += J[i * nv + k] * dqfrc[k];
+    u[i] = v;
+    daref[i] = act[i] ? D[i] * v : 0.0;
+  }
+  for (int i = 0; i < m; ++i)
+    for (int k = 0; k < nv; ++k)
+      dJ[i * nv + k] = -(f[i] * dqfrc[k] + daref[i] * a[k]);
+done:
+  free(w);
+  return status;
+}
+
+/* Residual r(a), forces f and active set at a given a (for invariants). */
+double oracle_residual(int nv, int m, const double *M, const double *J,
+                       const double *qfrc, const double *aref, const double *D,
+                       const double *a, double *r, double *f, uint8_t *act) {
+  problem P = {nv, m, M, J, qfrc, aref, D};
+  double *w = (double *)calloc((size_t)(m + 2 * nv + 4), sizeof(double));
+  double scale = residual(&P, a, w, act, f, w + m, w + m + nv, r);
+  free(w);
+  return scale;
+}
+
+/* Objective L(a) of Eq. 5 (pyramidal rows); a0 = M^-1 qfrc is recomputed. */
+double oracle_objective(int nv, int m, const double *M, const double *J,
+                        const double *qfrc, const double *aref, const double *D,
+                        const double *a) {
+  double *w = (double *)calloc((size_t)(nv * nv + 2 * nv + 4), sizeof(double));
+  double *H = w, *a0 = H + nv * nv, *d = a0 + nv;
+  memcpy(H, M, sizeof(double) * nv * nv);
+  if (chol(nv, H)) { free(w); return NAN; }
+  memcpy(a0, qfrc, sizeof(double) * nv);
+  chol_solve(nv, H, a0);
+  for (int j = 0; j < nv; ++j) d[j] = a[j] - a0[j];
+  double v = 0.0;
+  for (int j = 0; j < nv; ++j)
+    for (int k = 0; k < nv; ++k) v += 0.5 * d[j] * M[j * nv + k] * d[k];
+  for (int i = 0; i < m; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < nv; ++k) s += J[i * nv + k] * a[k];
+    s -= aref[i];
+    if (s < 0.0) v += 0.5 * D[i] * s * s;
+  }
+  free(w);
+  return v;
+}
+
+/* Batched forward + adjoint over instances [lo, hi) of a ragged batch laid out
+ * like the C ABI (offsets in elements).  Inputs are float32 widened to double
+ * by the caller.  Per instance: a, act, status, iters, dqfrc, daref, dJ.
+ * g may be NULL (forward only). */
+void oracle_batch(int lo, int hi, const int32_t *nv, const int32_t *m,
+                  const int64_t *off_M, const int64_t *off_J,
+                  const int64_t *off_v, const int64_t *off_r, const double *M,
+                  const double *J, const double *qfrc, const double *aref,
+                  const double *D, const double *g, double tol, int max_iter,
+                  double *a, uint8_t *act, int32_t *status, int32_t *iters,
+                  double *dqfrc, double *daref, double *dJ) {
+  for (int b = lo; b < hi; ++b) {
+    int it = 0;
+    const double *Mb = M + off_M[b], *Jb = J + off_J[b];
+    status[b] = oracle_solve(nv[b], m[b], Mb, Jb, qfrc + off_v[b],
+                             aref + off_r[b], D + off_r[b], NULL, tol, max_iter,
+                             a + off_v[b], act + off_r[b], &it);
+    iters[b] = it;
+    if (g && status[b] != OR_BADSHAPE && status[b] != OR_CHOLFAIL &&
+        status[b] != OR_NONFINITE) {
+      int s2 = oracle_adjoint(nv[b], m[b], Mb, Jb, qfrc + off_v[b],
+                              aref + off_r[b], D + off_r[b], a + off_v[b],
+                              g + off_v[b], dqfrc + off_v[b], daref + off_r[b],
+                              dJ + off_J[b], act + off_r[b]);
+      if (s2) status[b] = s2;
+    }
+  }
+}
+
+/* The exact line search on its own, for pinning it: returns the minimiser of
+ * phi(alpha) = L(a + alpha p) over alpha > 0. */
+double oracle_line_search(int nv, int m, const double *M, const double *J,
+                          const double *qfrc, const double *aref,
+                          const double *D, const double *a, const double *p) {
+  problem P = {nv, m, M, J, qfrc, aref, D};
+  double *w = (double *)calloc((size_t)(4 * m + 4 * nv + 4), sizeof(double));
+  breakpoint *bp = (breakpoint *)calloc((size_t)m + 1, sizeof(breakpoint));
+  uint8_t *act = (uint8_t *)calloc((size_t)m + 1, 1);
+  double *jar = w, *f = jar + m, *s = f + m, *Ma = s + m, *Jtf = Ma + nv;
+  double *r = Jtf + nv;
+  residual(&P, a, jar, act, f, Ma, Jtf, r);
+  double alpha = line_search(&P, a, p, jar, Ma, s, bp);
+  free(w);
+  free(bp);
+  free(act);
+  return alpha;
+}
