@@ -1,0 +1,165 @@
+/*
+ * contact_solve.h -- C ABI of the B300 batched regularised smooth-contact solve
+ * and its implicit-function-theorem (IFT) adjoint.
+ *
+ * The operation (Section III of "Amortising Trajectory Optimisation for
+ * Residual MPC via Implicit Contact Differentiation"), per instance b:
+ *
+ *   a0  = M^-1 qfrc                                            (Eq. 1)
+ *   a*  = argmin_a 1/2 (a-a0)^T M (a-a0) + 1/2 sum_i D_i min(jar_i, 0)^2,
+ *         jar = J a - aref                                     (Eq. 5, with the
+ *         cone term read as four one-sided pyramid rows per contact and
+ *         D = R^-1 of Eq. 4)
+ *   found by Newton steps on the stationarity residual
+ *         r(a) = M a - qfrc + J^T f,  f = D . min(jar, 0)      (Eqs. 6, 8)
+ *   with H = M + J^T diag(D . [jar < 0]) J                     (Eq. 9)
+ *   and an exact line search on the piecewise-quadratic cost   (Eq. 10).
+ *   Adjoint at the returned a, with F_a = H (symmetric)        (Eq. 17):
+ *         H w = g,  dL/dqfrc = w,  dL/daref = D_act . (J w),
+ *         dL/dJ = -(f w^T + (D_act . J w) a^T).
+ *
+ * Conventions shared by every entry point:
+ *  - All float data are IEEE binary32, row-major, packed per instance at the
+ *    element offsets of the instance table (cs_inst).  M is nv x nv and must be
+ *    symmetric positive definite; J is m x nv (rows grouped four per contact);
+ *    nv-vectors (qfrc, a, g, dqfrc, a_lo) sit at off_v; m-vectors (aref, D,
+ *    daref, act) at off_r; dJ uses J's layout.  Offsets that are multiples of
+ *    4 elements let the kernels use 16-byte loads; any offset is accepted.
+ *  - Pointers marked "device" must be CUDA device (or managed) memory on the
+ *    current device; the caller owns every buffer it passes and keeps it alive
+ *    until the work on `stream` has completed.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous: they validate on the host, enqueue kernels and return;
+ *    outputs are valid once the stream has been synchronised.
+ *  - Return codes are CS_OK (0) or a negative CS_E* code; nothing is thrown
+ *    across the ABI.  cs_last_error() describes the last failure of the
+ *    calling thread.  Per-instance numerical outcomes (CS_ST_*) are written to
+ *    the status array, never returned.
+ *  - Supported sizes: 1 <= nv <= 32 and 0 <= m <= 256 per instance (one warp
+ *    per instance).  An instance outside them gets CS_ST_BADSHAPE.
+ */
+#ifndef CONTACT_SOLVE_H
+#define CONTACT_SOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------- */
+#define CS_OK 0
+#define CS_EINVAL (-1)       /* bad argument, shape or pointer */
+#define CS_ECUDA (-2)        /* CUDA runtime error (cs_last_error has text) */
+#define CS_ENOMEM (-3)       /* device or host allocation failed */
+#define CS_EBUSY (-4)        /* serving: no free slot or arena bytes now */
+#define CS_ENOTFOUND (-5)    /* serving: unknown or already collected ticket */
+#define CS_EUNSUPPORTED (-6) /* sizes beyond the compiled kernels */
+#define CS_PENDING 1         /* serving: result not ready yet */
+
+/* ---- per-instance status (written to the status array) ------------------ */
+#define CS_ST_OK 0         /* converged (residual or step test) */
+#define CS_ST_MAXITER 1    /* Newton step cap max_iter reached */
+#define CS_ST_CHOLFAIL 2   /* non-positive pivot in a Cholesky factor */
+#define CS_ST_NONFINITE 3  /* NaN or Inf in the residual */
+#define CS_ST_BADSHAPE 4   /* nv/m outside the supported range, or offsets
+                              outside the batch totals */
+#define CS_ST_NOPROGRESS 5 /* the Newton direction was not a descent one */
+
+/* One instance of a ragged batch (40 bytes).  Offsets are in elements. */
+typedef struct cs_inst {
+  int32_t nv;    /* degrees of freedom */
+  int32_t m;     /* constraint rows, 4 per contact */
+  int64_t off_M; /* M (nv*nv) in cs_batch.M; factor slot in cs_state.L */
+  int64_t off_J; /* J (m*nv) in cs_batch.J; dJ in the output */
+  int64_t off_v; /* nv-vectors: qfrc, g, a, a_lo, dqfrc */
+  int64_t off_r; /* m-vectors: aref, D, daref, act */
+} cs_inst;
+
+/* A ragged batch.  inst and the five data arrays are device pointers.  The
+ * totals are the element counts of the arrays; every instance's block must
+ * lie inside them (checked on the device, CS_ST_BADSHAPE otherwise).
+ * nv_max and m_max are host-side bounds over the batch (they pick the
+ * kernel); an instance above them is marked CS_ST_BADSHAPE. */
+typedef struct cs_batch {
+  int32_t n;             /* number of instances (0 is a no-op) */
+  int32_t nv_max;        /* max nv over the batch, 1..32 */
+  int32_t m_max;         /* max m over the batch, 0..256 */
+  int32_t reserved;
+  const cs_inst* inst;   /* device, n entries */
+  const float* M;        /* device */
+  const float* J;        /* device */
+  const float* qfrc;     /* device */
+  const float* aref;     /* device */
+  const float* D;        /* device, entries > 0 */
+  int64_t total_M, total_J, total_v, total_r;
+} cs_batch;
+
+/* Solver options. */
+typedef struct cs_options {
+  float tol;           /* stop when ||r||_inf <= tol * max(1,|qfrc|,|Ma|,|J^T f|) */
+  int32_t max_iter;    /* Newton step cap K (>= 0; 0 returns a0) */
+  int32_t keep_factor; /* fwd: 1 = store the Cholesky factor of H(a*) for the
+                          adjoint; 0 = store only a*, a_lo and the active set
+                          and refactor in the adjoint (less memory) */
+  int32_t warps_per_block; /* 0 = library choice (autotuned), else 1..8 */
+} cs_options;
+
+/* Adjoint state written by cs_solve_fwd and read by cs_solve_adjoint.  All
+ * arrays are caller-allocated device memory laid out like the batch.  Its
+ * size does not depend on the number of Newton iterations. */
+typedef struct cs_state {
+  float* a_lo;     /* device, total_v: low part of a* (a* = a + a_lo) */
+  uint8_t* act;    /* device, total_r: active set at a* (1 = jar < 0) */
+  float* L;        /* device, total_M: packed lower rows of chol(H(a*)),
+                      nv(nv+1)/2 per instance at off_M; may be NULL when
+                      keep_factor == 0 */
+  int32_t* status; /* device, n: CS_ST_* */
+  int32_t* iters;  /* device, n: Newton steps taken */
+} cs_state;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int cs_version(void);
+
+/* Text for a CS_* return code. */
+const char* cs_strerror(int code);
+
+/* Text of the calling thread's last failure ("" if none). */
+const char* cs_last_error(void);
+
+/* Forward solve (Eqs. 1, 5-10).  Writes a (device, total_v) and the adjoint
+ * state.  Returns CS_EINVAL for a NULL/inconsistent argument, CS_ECUDA on a
+ * launch failure. */
+int cs_solve_fwd(const cs_batch* batch, const cs_options* opt, float* a,
+                 const cs_state* state, void* stream);
+
+/* IFT adjoint (Eq. 17) at the state left by cs_solve_fwd for the same batch
+ * and the same a.  g (device, total_v) is dL/da.  Writes dqfrc (total_v),
+ * daref (total_r) and dJ (total_J), all device.  With keep_factor == 0 (or
+ * state->L == NULL) the factor is rebuilt from the stored active set. */
+int cs_solve_adjoint(const cs_batch* batch, const cs_options* opt,
+                     const float* a, const cs_state* state, const float* g,
+                     float* dqfrc, float* daref, float* dJ, void* stream);
+
+/* Bytes of device workspace cs_solve_fused needs for n instances. */
+size_t cs_fused_workspace_bytes(int32_t n);
+
+/* Fused forward + adjoint for a known cotangent g: one persistent launch
+ * whose warps claim instances from a work counter kept in `workspace`
+ * (device, >= cs_fused_workspace_bytes(n) bytes, 16-byte aligned; the call
+ * resets the counter on `stream` first).  `order` (device, n entries, or
+ * NULL for 0..n-1) is the claim order.  Writes a, dqfrc, daref, dJ (device)
+ * and status, iters (device, n).  Nothing is kept between the two halves in
+ * global memory. */
+int cs_solve_fused(const cs_batch* batch, const cs_options* opt,
+                   const float* g, const int32_t* order, float* a,
+                   float* dqfrc, float* daref, float* dJ, int32_t* status,
+                   int32_t* iters, void* workspace, size_t workspace_bytes,
+                   void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CONTACT_SOLVE_H */

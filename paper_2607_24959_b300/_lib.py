@@ -1,0 +1,109 @@
+"""ctypes view of the C ABI in ``include/contact_solve.h``.
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels of
+``libcs_b300.so``.  Loading fails loudly if the library is missing; there is
+no CPU fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcs_b300.so")
+
+c_int32 = ctypes.c_int32
+c_int64 = ctypes.c_int64
+c_float = ctypes.c_float
+c_void_p = ctypes.c_void_p
+c_size_t = ctypes.c_size_t
+
+CS_OK = 0
+CS_EINVAL = -1
+CS_ECUDA = -2
+CS_ENOMEM = -3
+CS_EBUSY = -4
+CS_ENOTFOUND = -5
+CS_EUNSUPPORTED = -6
+CS_PENDING = 1
+
+ST_OK, ST_MAXITER, ST_CHOLFAIL, ST_NONFINITE, ST_BADSHAPE, ST_NOPROGRESS = range(6)
+STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "CHOLFAIL", 3: "NONFINITE",
+                4: "BADSHAPE", 5: "NOPROGRESS"}
+
+
+class CsBatch(ctypes.Structure):
+    _fields_ = [("n", c_int32), ("nv_max", c_int32), ("m_max", c_int32),
+                ("reserved", c_int32), ("inst", c_void_p), ("M", c_void_p),
+                ("J", c_void_p), ("qfrc", c_void_p), ("aref", c_void_p),
+                ("D", c_void_p), ("total_M", c_int64), ("total_J", c_int64),
+                ("total_v", c_int64), ("total_r", c_int64)]
+
+
+class CsOptions(ctypes.Structure):
+    _fields_ = [("tol", c_float), ("max_iter", c_int32), ("keep_factor", c_int32),
+                ("warps_per_block", c_int32)]
+
+
+class CsState(ctypes.Structure):
+    _fields_ = [("a_lo", c_void_p), ("act", c_void_p), ("L", c_void_p),
+                ("status", c_void_p), ("iters", c_void_p)]
+
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "cs_version": (ctypes.c_int, []),
+    "cs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "cs_last_error": (ctypes.c_char_p, []),
+    "cs_solve_fwd": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
+                                    c_void_p, ctypes.POINTER(CsState), c_void_p]),
+    "cs_solve_adjoint": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
+                                        c_void_p, ctypes.POINTER(CsState), c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_void_p]),
+    "cs_fused_workspace_bytes": (c_size_t, [c_int32]),
+    "cs_solve_fused": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
+                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                                      c_void_p]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libcs_b300.so (raises if it is missing or lacks a symbol)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"CUDA library {p} is missing: build it with "
+                "`python -m paper_2607_24959_b300.build` (no CPU fallback exists)")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def register(name, restype, argtypes):
+    """Declare another entry point's signature (used by optional modules)."""
+    _SIGS[name] = (restype, argtypes)
+    if _lib is not None:
+        fn = getattr(_lib, name)
+        fn.restype = restype
+        fn.argtypes = argtypes
+
+
+def check(rc: int, what: str) -> int:
+    if rc < 0:
+        lib = load()
+        msg = lib.cs_last_error().decode(errors="replace")
+        raise RuntimeError(f"{what} failed: {lib.cs_strerror(rc).decode()} ({rc}): {msg}")
+    return rc

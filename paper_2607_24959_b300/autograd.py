@@ -1,0 +1,60 @@
+"""``torch.autograd.Function`` around the solve: the backward pass is the IFT
+adjoint of Eq. 17, never an unrolled solver trace.
+
+Forward runs ``cs_solve_fwd`` and keeps only the adjoint state (a*, a_lo, the
+active set and, by default, the Cholesky factor of H(a*)), whose size does not
+depend on the number of Newton iterations.  Backward runs
+``cs_solve_adjoint`` on grad_a and returns dL/dJ, dL/dqfrc and dL/daref.  M and
+D are treated as constants (their cotangents are not produced).
+
+With ``keep_factor=False`` the factor is not stored; the backward rebuilds it
+from the stored active set (less memory, one extra factorisation).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import solver
+
+
+class ContactSolve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, batch: solver.DeviceBatch, M, J, qfrc, aref, D,
+                tol=solver.DEFAULT_TOL, max_iter=solver.DEFAULT_MAX_ITER,
+                keep_factor=True):
+        b = batch.with_data(M=M.detach().contiguous(), J=J.detach().contiguous(),
+                            qfrc=qfrc.detach().contiguous(),
+                            aref=aref.detach().contiguous(), D=D.detach().contiguous())
+        a, state = solver.solve_fwd(b, tol=tol, max_iter=max_iter,
+                                    keep_factor=keep_factor)
+        ctx.batch = b
+        ctx.state = state
+        ctx.tol = tol
+        ctx.max_iter = max_iter
+        ctx.save_for_backward(a)
+        ctx.mark_non_differentiable()
+        return a
+
+    @staticmethod
+    def backward(ctx, grad_a):
+        (a,) = ctx.saved_tensors
+        dq, dr, dJ = solver.solve_adjoint(ctx.batch, a, ctx.state,
+                                          grad_a.contiguous(), tol=ctx.tol,
+                                          max_iter=ctx.max_iter)
+        b = ctx.batch
+        dJ = dJ[:b.J.numel()].view_as(b.J) if b.J.numel() else torch.zeros_like(b.J)
+        dr = dr[:b.aref.numel()].view_as(b.aref) if b.aref.numel() else torch.zeros_like(b.aref)
+        dq = dq[:b.qfrc.numel()].view_as(b.qfrc)
+        return None, None, dJ, dq, dr, None, None, None, None
+
+
+def contact_solve(batch: solver.DeviceBatch, M=None, J=None, qfrc=None, aref=None,
+                  D=None, tol=solver.DEFAULT_TOL, max_iter=solver.DEFAULT_MAX_ITER,
+                  keep_factor=True):
+    """a* for the batch; differentiable w.r.t. J, qfrc and aref."""
+    return ContactSolve.apply(batch, batch.M if M is None else M,
+                              batch.J if J is None else J,
+                              batch.qfrc if qfrc is None else qfrc,
+                              batch.aref if aref is None else aref,
+                              batch.D if D is None else D, tol, max_iter,
+                              keep_factor)

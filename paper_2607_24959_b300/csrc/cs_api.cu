@@ -1,0 +1,234 @@
+// cs_api.cu -- host side of the C ABI declared in include/contact_solve.h:
+// argument validation, kernel selection over the compiled (NV, MT) grid,
+// launch geometry, and error reporting.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "contact_solve.h"
+#include "cs_host.h"
+#include "cs_warp.cuh"
+
+namespace cs {
+
+static thread_local char g_last_error[512] = "";
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* where) {
+  return set_error(CS_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Compiled buckets.  nv is padded up to the bucket; m up to 32 * MT.
+static const int kNvBuckets[] = {3, 9, 18, 32};
+static const int kMtBuckets[] = {1, 2, 4, 8};
+
+int nv_bucket(int nv) {
+  for (int b : kNvBuckets)
+    if (nv <= b) return b;
+  return -1;
+}
+int mt_bucket(int m) {
+  for (int t : kMtBuckets)
+    if (m <= 32 * t) return t;
+  return -1;
+}
+
+struct DevInfo {
+  int sms = 0;
+  size_t smem_optin = 0;
+};
+static DevInfo dev_info() {
+  static std::mutex mu;
+  static DevInfo cache[16];
+  static bool have[16] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return DevInfo{148, 227 * 1024};
+  std::lock_guard<std::mutex> lk(mu);
+  if (!have[dev]) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) {
+      cache[dev].sms = p.multiProcessorCount;
+      cache[dev].smem_optin = p.sharedMemPerBlockOptin;
+    } else {
+      cache[dev].sms = 148;
+      cache[dev].smem_optin = 227 * 1024;
+    }
+    have[dev] = true;
+  }
+  return cache[dev];
+}
+
+int device_sm_count() { return dev_info().sms; }
+size_t device_smem_optin() { return dev_info().smem_optin; }
+
+cudaError_t launch_warp(int mode, int nv_max, int m_max, const csk::Params& P,
+                        const LaunchCfg& cfg, cudaStream_t s, KernelInfo* info) {
+  int nvb = nv_bucket(nv_max), mt = mt_bucket(m_max);
+  if (nvb < 0 || mt < 0) return cudaErrorInvalidValue;
+  switch (nvb) {
+    case 3: return launch_nv<3>(mode, mt, P, cfg, s, info);
+    case 9: return launch_nv<9>(mode, mt, P, cfg, s, info);
+    case 18: return launch_nv<18>(mode, mt, P, cfg, s, info);
+    default: return launch_nv<32>(mode, mt, P, cfg, s, info);
+  }
+}
+
+int check_batch(const cs_batch* b, const cs_options* o) {
+  if (!b || !o) return set_error(CS_EINVAL, "batch and options must not be NULL");
+  if (b->n < 0) return set_error(CS_EINVAL, "n = %d < 0", b->n);
+  if (b->n == 0) return CS_OK;
+  if (b->nv_max < 1 || b->nv_max > 32)
+    return set_error(CS_EUNSUPPORTED, "nv_max = %d outside 1..32", b->nv_max);
+  if (b->m_max < 0 || b->m_max > 256)
+    return set_error(CS_EUNSUPPORTED, "m_max = %d outside 0..256", b->m_max);
+  if (!b->inst || !b->M || !b->qfrc)
+    return set_error(CS_EINVAL, "inst, M and qfrc must not be NULL");
+  if (b->m_max > 0 && (!b->J || !b->aref || !b->D))
+    return set_error(CS_EINVAL, "J, aref and D must not be NULL when m_max > 0");
+  if (b->total_M < 0 || b->total_J < 0 || b->total_v < 0 || b->total_r < 0)
+    return set_error(CS_EINVAL, "negative array totals");
+  if (!(o->tol >= 0.f)) return set_error(CS_EINVAL, "tol must be >= 0");
+  if (o->max_iter < 0 || o->max_iter > 100000)
+    return set_error(CS_EINVAL, "max_iter = %d outside 0..100000", o->max_iter);
+  if (o->warps_per_block < 0 || o->warps_per_block > 8)
+    return set_error(CS_EINVAL, "warps_per_block = %d outside 0..8", o->warps_per_block);
+  return CS_OK;
+}
+
+csk::Params make_params(const cs_batch* b, const cs_options* o) {
+  csk::Params P;
+  memset(&P, 0, sizeof(P));
+  P.n = b->n;
+  P.inst = b->inst;
+  P.M = b->M;
+  P.J = b->J;
+  P.qfrc = b->qfrc;
+  P.aref = b->aref;
+  P.D = b->D;
+  P.total_M = b->total_M;
+  P.total_J = b->total_J;
+  P.total_v = b->total_v;
+  P.total_r = b->total_r;
+  P.tol = o->tol;
+  P.max_iter = o->max_iter;
+  P.keep_factor = o->keep_factor;
+  return P;
+}
+
+}  // namespace cs
+
+using namespace cs;
+
+extern "C" {
+
+int cs_version(void) { return 100; }
+
+const char* cs_strerror(int code) {
+  switch (code) {
+    case CS_OK: return "ok";
+    case CS_EINVAL: return "invalid argument";
+    case CS_ECUDA: return "CUDA error";
+    case CS_ENOMEM: return "out of memory";
+    case CS_EBUSY: return "busy: no free slot or arena space";
+    case CS_ENOTFOUND: return "unknown ticket";
+    case CS_EUNSUPPORTED: return "unsupported size";
+    case CS_PENDING: return "pending";
+    default: return "unknown error code";
+  }
+}
+
+const char* cs_last_error(void) { return g_last_error; }
+
+int cs_solve_fwd(const cs_batch* batch, const cs_options* opt, float* a, const cs_state* st,
+                 void* stream) {
+  int rc = check_batch(batch, opt);
+  if (rc != CS_OK || batch->n == 0) return rc;
+  if (!a || !st || !st->a_lo || !st->status || !st->iters || (batch->m_max > 0 && !st->act))
+    return set_error(CS_EINVAL, "a and the state arrays must not be NULL");
+  csk::Params P = make_params(batch, opt);
+  P.a = a;
+  P.a_lo = st->a_lo;
+  P.act = st->act;
+  P.Lst = opt->keep_factor ? st->L : nullptr;
+  P.status = st->status;
+  P.iters = st->iters;
+  LaunchCfg cfg;
+  cfg.warps_per_block = opt->warps_per_block;
+  cudaError_t e = launch_warp(csk::MODE_FWD, batch->nv_max, batch->m_max, P, cfg,
+                              (cudaStream_t)stream, nullptr);
+  return e == cudaSuccess ? CS_OK : cuda_error(e, "cs_solve_fwd launch");
+}
+
+int cs_solve_adjoint(const cs_batch* batch, const cs_options* opt, const float* a,
+                     const cs_state* st, const float* g, float* dqfrc, float* daref, float* dJ,
+                     void* stream) {
+  int rc = check_batch(batch, opt);
+  if (rc != CS_OK || batch->n == 0) return rc;
+  if (!a || !st || !st->a_lo || !st->status || !st->iters || !g || !dqfrc ||
+      (batch->m_max > 0 && (!st->act || !daref || !dJ)))
+    return set_error(CS_EINVAL, "a, g, the outputs and the state arrays must not be NULL");
+  csk::Params P = make_params(batch, opt);
+  P.a = const_cast<float*>(a);
+  P.g = g;
+  P.a_lo = st->a_lo;
+  P.act = st->act;
+  P.Lst = opt->keep_factor ? st->L : nullptr;
+  P.status = st->status;
+  P.iters = st->iters;
+  P.dqfrc = dqfrc;
+  P.daref = daref;
+  P.dJ = dJ;
+  LaunchCfg cfg;
+  cfg.warps_per_block = opt->warps_per_block;
+  cudaError_t e = launch_warp(csk::MODE_ADJ, batch->nv_max, batch->m_max, P, cfg,
+                              (cudaStream_t)stream, nullptr);
+  return e == cudaSuccess ? CS_OK : cuda_error(e, "cs_solve_adjoint launch");
+}
+
+size_t cs_fused_workspace_bytes(int32_t n) {
+  (void)n;
+  return 256;
+}
+
+int cs_solve_fused(const cs_batch* batch, const cs_options* opt, const float* g,
+                   const int32_t* order, float* a, float* dqfrc, float* daref, float* dJ,
+                   int32_t* status, int32_t* iters, void* workspace, size_t workspace_bytes,
+                   void* stream) {
+  int rc = check_batch(batch, opt);
+  if (rc != CS_OK || batch->n == 0) return rc;
+  if (!g || !a || !dqfrc || !status || !iters || (batch->m_max > 0 && (!daref || !dJ)))
+    return set_error(CS_EINVAL, "g and the output arrays must not be NULL");
+  if (!workspace || workspace_bytes < cs_fused_workspace_bytes(batch->n) ||
+      (reinterpret_cast<uintptr_t>(workspace) & 15))
+    return set_error(CS_EINVAL, "workspace must be >= %zu bytes and 16-byte aligned",
+                     cs_fused_workspace_bytes(batch->n));
+  csk::Params P = make_params(batch, opt);
+  P.g = g;
+  P.a = a;
+  P.dqfrc = dqfrc;
+  P.daref = daref;
+  P.dJ = dJ;
+  P.status = status;
+  P.iters = iters;
+  P.counter = reinterpret_cast<int32_t*>(workspace);
+  P.order = order;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return cuda_error(e, "cs_solve_fused counter reset");
+  LaunchCfg cfg;
+  cfg.warps_per_block = opt->warps_per_block;
+  e = launch_warp(csk::MODE_FUSED, batch->nv_max, batch->m_max, P, cfg, s, nullptr);
+  return e == cudaSuccess ? CS_OK : cuda_error(e, "cs_solve_fused launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,812 @@
+// cs_warp.cuh -- one-warp-per-instance contact solver (device code).
+//
+// A warp owns one instance at a time.  Its M, J and D sit in the warp's slice
+// of shared memory; every per-row quantity (jar, J p, D, aref) is spread over
+// the lanes as "row i = lane + 32 t, t < MT"; every nv-vector is spread as
+// "element j on lane j" and broadcast through a small shared buffer.
+//
+// Arithmetic (Section III of the paper):
+//  * residual r = M a - qfrc + J^T f, f = D . min(J a - aref, 0) (Eqs. 6, 8).
+//    a is carried as an unevaluated float pair (hi + lo) and r, jar are
+//    accumulated with error-free transformations (TwoSum / TwoProd), so the
+//    contact forces f keep their accuracy when a stiff row has |jar| << |J a|;
+//  * H = M + sum_{i active} D_i J_i^T J_i (Eq. 9), a warp Cholesky in
+//    registers (lane j holds row j), triangular solves by shuffles;
+//  * p = -H^-1 r and an exact line search on the piecewise-linear derivative
+//    of phi(alpha) = L(a + alpha p) (Eq. 10): safeguarded Newton on phi' that
+//    stops when no breakpoint separates the trial point from its Newton
+//    point, which makes the returned alpha the exact root;
+//  * the IFT adjoint H w = g (Eq. 17), refined with compensated residuals so
+//    that D_act . (J w) keeps its accuracy for stiff rows.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "contact_solve.h"
+
+namespace csk {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kLineSearchMax = 64;  // exact line-search trial points
+constexpr int kAdjointRefineMax = 8;
+// Step test: a step that moves a by <= kStepTol |a| and the active forces by
+// <= kForceTol |f| with an unchanged active set means the fp32 Newton /
+// refinement iteration has reached its attainable accuracy.
+constexpr float kStepTol = 1.0e-7f;
+constexpr float kForceTol = 1.0e-6f;
+
+// ---------------------------------------------------------------- EFT helpers
+// __f*_rn intrinsics are never contracted into FMAs, which keeps the
+// error-free transformations exact.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+// (s, c) += x * (yh + yl)
+__device__ __forceinline__ void dot2(float& s, float& c, float x, float yh, float yl) {
+  float p = __fmul_rn(x, yh);
+  float pe = __fmaf_rn(x, yh, -p);
+  float t, te;
+  two_sum(s, p, t, te);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(te, __fmaf_rn(x, yl, pe)));
+}
+// (s, c) += x * y
+__device__ __forceinline__ void dot2s(float& s, float& c, float x, float y) {
+  float p = __fmul_rn(x, y);
+  float pe = __fmaf_rn(x, y, -p);
+  float t, te;
+  two_sum(s, p, t, te);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(te, pe));
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// ------------------------------------------------------------------ geometry
+template <int NV, int MT>
+struct Geo {
+  static_assert(NV >= 1 && NV <= 32, "one lane per row of H");
+  static constexpr int MCAP = 32 * MT;               // rows per instance
+  static constexpr int BS = (NV + 6) / 7;            // H block edge
+  static constexpr int NB = (NV + BS - 1) / BS;      // blocks per edge (<= 7)
+  static constexpr int NBLK = NB * (NB + 1) / 2;     // lower blocks (<= 28)
+  static constexpr int NVP = NB * BS;                // padded columns
+  static constexpr int JS = NVP | 1;                 // J row stride (odd)
+  static constexpr int MS = NV | 1;                  // M/L row stride (odd)
+  // shared-memory slice of one warp, in 4-byte words
+  static constexpr int oM = 0;                       // M   NV x MS
+  static constexpr int oL = oM + NV * MS;            // H/L NV x MS
+  static constexpr int oJ = oL + NV * MS;            // J   MCAP x JS
+  static constexpr int oD = oJ + MCAP * JS;          // D   MCAP
+  static constexpr int oF = oD + MCAP;               // f   MCAP
+  static constexpr int oLam = oF + MCAP;             // lambda = D_act J w
+  static constexpr int oIdx = oLam + MCAP;           // active rows (int)
+  static constexpr int oVec = oIdx + MCAP;           // 6 broadcast vectors
+  static constexpr int kVec = 6;
+  static constexpr int kWords = oVec + kVec * 32;
+  static constexpr int kBytes = ((kWords * 4) + 127) & ~127;
+};
+
+enum VecSlot { V_AH = 0, V_AL = 1, V_P = 2, V_WH = 3, V_WL = 4, V_X = 5 };
+
+// Kernel parameters (one struct, passed by value).
+struct Params {
+  int32_t n;
+  const cs_inst* inst;
+  const float *M, *J, *qfrc, *aref, *D, *g;
+  int64_t total_M, total_J, total_v, total_r;
+  float* a;                 // out (fwd, fused) / in (adjoint)
+  float *dqfrc, *daref, *dJ;
+  float* a_lo;              // state
+  uint8_t* act;             // state
+  float* Lst;               // state factor (packed lower rows) or null
+  int32_t *status, *iters;
+  float tol;
+  int32_t max_iter;
+  int32_t keep_factor;
+  int32_t* counter;         // dynamic claim counter (fused) or null
+  const int32_t* order;     // claim order or null
+};
+
+enum Mode { MODE_FWD = 0, MODE_ADJ = 1, MODE_FUSED = 2 };
+
+template <int NV, int MT>
+struct WarpSolver {
+  using G = Geo<NV, MT>;
+  float* sm;   // warp slice
+  int lane;
+
+  // problem sizes of the current instance
+  int nv, m;
+  // row registers: row i = lane + 32 t
+  float aref_r[MT], D_r[MT], jar_r[MT], s_r[MT];
+  uint32_t act_bits;    // bit t: row lane+32t active at the current point
+  uint32_t fmask_bits;  // active set the factor in h[] belongs to
+  bool fmask_valid;
+  int nact;
+  // element registers (lane j < NV)
+  float ah, al;          // a = ah + al
+  float qf, gj;          // qfrc_j, g_j
+  float r, maq;          // r_j, (M a - qfrc)_j
+  float h[NV];           // row j of the current Cholesky factor
+  float dinv;            // 1 / L_jj
+  float fmax;            // max |f| at the current point
+  float qmax;            // max |qfrc|
+
+  __device__ __forceinline__ float* Ms() { return sm + G::oM; }
+  __device__ __forceinline__ float* Ls() { return sm + G::oL; }
+  __device__ __forceinline__ float* Js() { return sm + G::oJ; }
+  __device__ __forceinline__ float* Ds() { return sm + G::oD; }
+  __device__ __forceinline__ float* Fs() { return sm + G::oF; }
+  __device__ __forceinline__ float* Lam() { return sm + G::oLam; }
+  __device__ __forceinline__ int* Idx() { return reinterpret_cast<int*>(sm + G::oIdx); }
+  __device__ __forceinline__ float* Vec(int s) { return sm + G::oVec + 32 * s; }
+
+  __device__ __forceinline__ bool row_valid(int t) const { return lane + 32 * t < m; }
+
+  // Broadcast the lane-distributed vector v into slot s (lanes >= NV write 0).
+  __device__ __forceinline__ void put_vec(int s, float v) {
+    Vec(s)[lane] = (lane < NV) ? v : 0.f;
+    __syncwarp();
+  }
+
+  // ------------------------------------------------------------- loading
+  // Stage one instance into shared memory.  Instances with nv < NV are padded
+  // with identity rows of M and zero columns of J (the padded unknowns stay
+  // exactly zero and do not touch the real ones).
+  __device__ __forceinline__ bool load(const Params& P, const cs_inst& e) {
+    nv = e.nv;
+    m = e.m;
+    if (nv < 1 || nv > NV || m < 0 || m > G::MCAP) return false;
+    if (e.off_M < 0 || e.off_J < 0 || e.off_v < 0 || e.off_r < 0) return false;
+    if (e.off_M + (int64_t)nv * nv > P.total_M) return false;
+    if (e.off_J + (int64_t)m * nv > P.total_J) return false;
+    if (e.off_v + nv > P.total_v || e.off_r + m > P.total_r) return false;
+    const float* M = P.M + e.off_M;
+    const float* J = P.J + e.off_J;
+    float* Ms_ = Ms();
+    float* Js_ = Js();
+    for (int q = lane; q < NV * NV; q += 32) {
+      int rr = q / NV, cc = q - rr * NV;
+      float v = (rr < nv && cc < nv) ? __ldg(M + rr * nv + cc) : (rr == cc ? 1.f : 0.f);
+      Ms_[rr * G::MS + cc] = v;
+    }
+    const int mnv = m * nv;
+    if (nv == NV) {
+      if ((reinterpret_cast<uintptr_t>(J) & 15) == 0) {
+        const float4* J4 = reinterpret_cast<const float4*>(J);
+        for (int q = lane; q < (mnv >> 2); q += 32) {
+          float4 v = __ldg(J4 + q);
+          int b = 4 * q;
+          int rr = b / NV, cc = b - rr * NV;
+          float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            Js_[rr * G::JS + cc] = vv[u];
+            if (++cc == NV) { cc = 0; ++rr; }
+          }
+        }
+        for (int q = (mnv & ~3) + lane; q < mnv; q += 32) {
+          int rr = q / NV, cc = q - rr * NV;
+          Js_[rr * G::JS + cc] = __ldg(J + q);
+        }
+      } else {
+        for (int q = lane; q < mnv; q += 32) {
+          int rr = q / NV, cc = q - rr * NV;
+          Js_[rr * G::JS + cc] = __ldg(J + q);
+        }
+      }
+    } else {
+      for (int q = lane; q < mnv; q += 32) {
+        int rr = q / nv, cc = q - rr * nv;
+        Js_[rr * G::JS + cc] = __ldg(J + q);
+      }
+    }
+    // zero padded columns of real rows, and whole rows up to the next
+    // multiple of 32 (read by the row loops but never active)
+    const int mpad = min(G::MCAP, (m + 31) & ~31);
+    const int padc = G::JS - nv;
+    for (int q = lane; q < m * padc; q += 32) {
+      int rr = q / padc, cc = nv + (q - rr * padc);
+      Js_[rr * G::JS + cc] = 0.f;
+    }
+    for (int q = m * G::JS + lane; q < mpad * G::JS; q += 32) Js_[q] = 0.f;
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+      int i = lane + 32 * t;
+      bool v = i < m;
+      aref_r[t] = v ? __ldg(P.aref + e.off_r + i) : 0.f;
+      D_r[t] = v ? __ldg(P.D + e.off_r + i) : 0.f;
+      if (i < mpad) Ds()[i] = D_r[t];
+    }
+    qf = (lane < nv) ? __ldg(P.qfrc + e.off_v + lane) : 0.f;
+    qmax = warp_max(fabsf(qf));
+    __syncwarp();
+    return true;
+  }
+
+  // ------------------------------------------------------------- Cholesky
+  // Factor the matrix whose lower rows are in Ls() (row stride MS).  Lane j
+  // keeps row j of L in h[]; L is also written back to Ls() for the
+  // transposed solve.  Returns false on a non-positive pivot.
+  //
+  // Every update below is branch-free with a compile-time index: a predicated
+  // form such as "if (lane >= jj) h[jj] = ..." lets the compiler re-roll the
+  // unrolled loop into one over a lane-dependent bound, which moves h[] to
+  // local memory.  Entries above the diagonal (k > lane) hold don't-care
+  // values and are never read into the lower triangle.
+  __device__ __forceinline__ bool factor_from_Ls() {
+    float* L = Ls();
+    {
+      const float* Lr = L + min(lane, NV - 1) * G::MS;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) h[k] = Lr[k];
+    }
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float d = __shfl_sync(kFull, h[k], k);
+      ok = ok && (d > 0.f) && (d < CUDART_INF_F);
+      float sq = sqrtf(d);
+      float inv = 1.0f / sq;
+      dinv = (lane == k) ? inv : dinv;
+      h[k] = (lane == k) ? sq : h[k] * inv;
+#pragma unroll
+      for (int jj = k + 1; jj < NV; ++jj) {
+        float l = __shfl_sync(kFull, h[k], jj);
+        float lm = (lane >= jj) ? l : 0.f;
+        h[jj] = __fmaf_rn(-h[k], lm, h[jj]);
+      }
+    }
+    __syncwarp();
+    if (lane < NV) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) L[lane * G::MS + k] = h[k];
+    }
+    __syncwarp();
+    return ok;
+  }
+
+  // z = (L L^T)^-1 x, vectors spread one element per lane.
+  __device__ __forceinline__ float chol_solve(float x) {
+    const float* L = Ls();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      if (lane == k) x *= dinv;
+      float yk = __shfl_sync(kFull, x, k);
+      if (lane > k && lane < NV) x = __fmaf_rn(-h[k], yk, x);
+    }
+#pragma unroll
+    for (int k = NV - 1; k >= 0; --k) {
+      if (lane == k) x *= dinv;
+      float zk = __shfl_sync(kFull, x, k);
+      if (lane < k) x = __fmaf_rn(-L[k * G::MS + lane], zk, x);
+    }
+    return (lane < NV) ? x : 0.f;
+  }
+
+  // Cholesky of M (the factor for the empty active set).
+  __device__ __forceinline__ bool factor_M() {
+    const float* Mm = Ms();
+    float* L = Ls();
+    if (lane < NV) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        if (k <= lane) L[lane * G::MS + k] = Mm[lane * G::MS + k];
+    }
+    __syncwarp();
+    return factor_from_Ls();
+  }
+
+  // H = M + sum_{active} D_i J_i^T J_i (Eq. 9) into Ls(), then factor.
+  // Lane l < NBLK accumulates one BS x BS block of the lower triangle.
+  __device__ __forceinline__ bool assemble_and_factor() {
+    const float* Mm = Ms();
+    const float* Jm = Js();
+    const float* Dm = Ds();
+    const int* idx = Idx();
+    float* L = Ls();
+    if (lane < G::NBLK) {
+      int bj = 0;
+      while ((bj + 1) * (bj + 2) / 2 <= lane) ++bj;
+      int bk = lane - bj * (bj + 1) / 2;
+      float acc[G::BS][G::BS];
+#pragma unroll
+      for (int u = 0; u < G::BS; ++u)
+#pragma unroll
+        for (int v = 0; v < G::BS; ++v) acc[u][v] = 0.f;
+      const int cj = bj * G::BS, ck = bk * G::BS;
+      for (int q = 0; q < nact; ++q) {
+        int i = idx[q];
+        float d = Dm[i];
+        const float* Ji = Jm + i * G::JS;
+        float x[G::BS], y[G::BS];
+#pragma unroll
+        for (int u = 0; u < G::BS; ++u) x[u] = Ji[cj + u] * d;
+#pragma unroll
+        for (int v = 0; v < G::BS; ++v) y[v] = Ji[ck + v];
+#pragma unroll
+        for (int u = 0; u < G::BS; ++u)
+#pragma unroll
+          for (int v = 0; v < G::BS; ++v) acc[u][v] = __fmaf_rn(x[u], y[v], acc[u][v]);
+      }
+#pragma unroll
+      for (int u = 0; u < G::BS; ++u)
+#pragma unroll
+        for (int v = 0; v < G::BS; ++v) {
+          int rr = cj + u, cc = ck + v;
+          if (rr < NV && cc <= rr) L[rr * G::MS + cc] = Mm[rr * G::MS + cc] + acc[u][v];
+        }
+    }
+    __syncwarp();
+    bool ok = factor_from_Ls();
+    fmask_bits = act_bits;
+    fmask_valid = true;
+    return ok;
+  }
+
+  // True when the active set differs from the factored one on any lane.
+  __device__ __forceinline__ bool need_refactor() {
+    return __any_sync(kFull, !fmask_valid || (act_bits != fmask_bits));
+  }
+
+  // --------------------------------------------------------- residual
+  // At a = ah + al: jar (compensated), active set, f, active row list,
+  // r = M a - qfrc + J^T f (compensated), maq = M a - qfrc.
+  // Returns max|r|; *scale = max(1, |qfrc|, |Ma|, |J^T f|); *bad = non-finite.
+  __device__ __forceinline__ float residual(float* scale, bool* bad) {
+    put_vec(V_AH, ah);
+    put_vec(V_AL, al);
+    const float* Jm = Js();
+    const float* vh = Vec(V_AH);
+    const float* vl = Vec(V_AL);
+    float s[MT], c[MT];
+#pragma unroll
+    for (int t = 0; t < MT; ++t) { s[t] = 0.f; c[t] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float xh = vh[k], xl = vl[k];
+#pragma unroll
+      for (int t = 0; t < MT; ++t)
+        if (32 * t < m) dot2(s[t], c[t], Jm[(lane + 32 * t) * G::JS + k], xh, xl);
+    }
+    act_bits = 0;
+    float* F = Fs();
+    int* idx = Idx();
+    int base = 0;
+    float fm = 0.f;
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+      if (32 * t < m) {
+        float u, ue;
+        two_sum(s[t], -aref_r[t], u, ue);
+        jar_r[t] = u + (ue + c[t]);
+        bool on = row_valid(t) && jar_r[t] < 0.f;
+        float f = on ? D_r[t] * jar_r[t] : 0.f;
+        if (row_valid(t)) F[lane + 32 * t] = f;
+        fm = fmaxf(fm, fabsf(f));
+        unsigned bal = __ballot_sync(kFull, on);
+        if (on) {
+          act_bits |= 1u << t;
+          idx[base + __popc(bal & ((1u << lane) - 1u))] = lane + 32 * t;
+        }
+        base += __popc(bal);
+      }
+    }
+    nact = base;
+    fmax = warp_max(fm);
+    __syncwarp();
+    // (M a)_j and (J^T f)_j, compensated, lane j
+    float ms = 0.f, mc = 0.f, js = 0.f, jc = 0.f;
+    if (lane < NV) {
+      const float* Mr = Ms() + lane * G::MS;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) dot2(ms, mc, Mr[k], vh[k], vl[k]);
+      for (int q = 0; q < nact; ++q) {
+        int i = idx[q];
+        dot2s(js, jc, Jm[i * G::JS + lane], F[i]);
+      }
+    }
+    float t1, e1, t2, e2;
+    two_sum(ms, -qf, t1, e1);
+    float lo1 = __fadd_rn(e1, mc);
+    maq = __fadd_rn(t1, lo1);
+    two_sum(t1, js, t2, e2);
+    r = __fadd_rn(t2, __fadd_rn(lo1, __fadd_rn(e2, jc)));
+    if (lane >= NV) { r = 0.f; maq = 0.f; }
+    float rm = warp_max(fabsf(r));
+    float sc = fmaxf(fmaxf(1.f, qmax), fmaxf(warp_max(fabsf(ms)), warp_max(fabsf(js))));
+    *scale = sc;
+    *bad = __any_sync(kFull, !(fabsf(r) < CUDART_INF_F)) || !(sc < CUDART_INF_F);
+    return rm;
+  }
+
+  // -------------------------------------------------------- line search
+  // alpha > 0 minimising phi(alpha) = L(a + alpha p) (Eq. 10), p spread per
+  // lane.  phi'(alpha) = c0 + alpha p^T M p + sum_i D_i s_i min(jar_i + alpha s_i, 0)
+  // with c0 = p^T (M a - qfrc) and s = J p; phi' is continuous, piecewise
+  // linear and strictly increasing.  Also leaves s_r = J p.
+  __device__ __forceinline__ float line_search(float p, float* dfmax) {
+    put_vec(V_P, p);
+    const float* Jm = Js();
+    const float* vp = Vec(V_P);
+#pragma unroll
+    for (int t = 0; t < MT; ++t) s_r[t] = 0.f;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float pk = vp[k];
+#pragma unroll
+      for (int t = 0; t < MT; ++t)
+        if (32 * t < m) s_r[t] = __fmaf_rn(Jm[(lane + 32 * t) * G::JS + k], pk, s_r[t]);
+    }
+    float Mp = 0.f;
+    if (lane < NV) {
+      const float* Mr = Ms() + lane * G::MS;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) Mp = __fmaf_rn(Mr[k], vp[k], Mp);
+    }
+    const float pMp = warp_sum(p * Mp);
+    const float c0 = warp_sum(p * maq);
+    float bp[MT];
+#pragma unroll
+    for (int t = 0; t < MT; ++t)
+      bp[t] = (row_valid(t) && s_r[t] != 0.f) ? -jar_r[t] / s_r[t] : CUDART_INF_F;
+    float alpha = 1.f, lo = 0.f, hi = CUDART_INF_F;
+    for (int it = 0; it < kLineSearchMax; ++it) {
+      float sum = 0.f, cp = 0.f, cm = 0.f;
+#pragma unroll
+      for (int t = 0; t < MT; ++t) {
+        if (row_valid(t)) {
+          float u = __fmaf_rn(alpha, s_r[t], jar_r[t]);
+          float ds = D_r[t] * s_r[t];
+          if (u < 0.f) sum = __fmaf_rn(ds, u, sum);
+          if (u < 0.f || (u == 0.f && s_r[t] < 0.f)) cp = __fmaf_rn(ds, s_r[t], cp);
+          if (u < 0.f || (u == 0.f && s_r[t] > 0.f)) cm = __fmaf_rn(ds, s_r[t], cm);
+        }
+      }
+      sum = warp_sum(sum);
+      cp = warp_sum(cp);
+      cm = warp_sum(cm);
+      const float d = c0 + alpha * pMp + sum;
+      if (d == 0.f) break;
+      float an, x0, x1;
+      if (d < 0.f) {
+        lo = alpha;
+        an = alpha - d / (pMp + cp);
+        x0 = alpha;
+        x1 = an;
+      } else {
+        hi = alpha;
+        an = alpha - d / (pMp + cm);
+        x0 = an;
+        x1 = alpha;
+      }
+      int cnt = 0;
+#pragma unroll
+      for (int t = 0; t < MT; ++t)
+        cnt += __popc(__ballot_sync(kFull, bp[t] > x0 && bp[t] < x1));
+      if (cnt == 0 && an > 0.f) { alpha = an; break; }
+      if (!(an > lo && an < hi)) an = (hi == CUDART_INF_F) ? 2.f * alpha : 0.5f * (lo + hi);
+      alpha = an;
+      if (it == kLineSearchMax - 1) alpha = (lo > 0.f) ? lo : alpha;
+    }
+    // largest change of an active force over the step
+    float df = 0.f;
+#pragma unroll
+    for (int t = 0; t < MT; ++t)
+      if ((act_bits >> t) & 1u) df = fmaxf(df, fabsf(D_r[t] * alpha * s_r[t]));
+    *dfmax = warp_max(df);
+    return alpha;
+  }
+
+  // a += dp, kept as a normalised float pair.
+  __device__ __forceinline__ void add_to_a(float dp) {
+    float s, e;
+    two_sum(ah, dp, s, e);
+    float lo = __fadd_rn(al, e);
+    ah = __fadd_rn(s, lo);
+    al = __fsub_rn(lo, __fsub_rn(ah, s));
+  }
+
+  // --------------------------------------------------------- forward solve
+  // Newton iteration (Eqs. 9-10) from a0 = M^-1 qfrc (Eq. 1).  Returns the
+  // status; *iters = Newton steps.  On return the residual quantities (jar,
+  // act_bits, f, active list) belong to the returned a.
+  __device__ __forceinline__ int forward(const Params& P, int* iters) {
+    *iters = 0;
+    if (!factor_M()) return CS_ST_CHOLFAIL;
+    fmask_bits = 0;
+    fmask_valid = true;
+    ah = chol_solve(qf);
+    al = 0.f;
+    uint32_t prev_bits = 0;
+    bool prev_small = false;
+    for (int k = 0;; ++k) {
+      float scale;
+      bool bad;
+      float rmax = residual(&scale, &bad);
+      if (bad) return CS_ST_NONFINITE;
+      if (rmax <= P.tol * scale) return CS_ST_OK;
+      bool same = !__any_sync(kFull, act_bits != prev_bits);
+      if (k > 0 && same && prev_small) return CS_ST_OK;
+      if (k >= P.max_iter) return CS_ST_MAXITER;
+      if (need_refactor())
+        if (!assemble_and_factor()) return CS_ST_CHOLFAIL;
+      float p = -chol_solve(r);
+      float ptr = warp_sum(p * r);
+      float amax = warp_max(fabsf(ah));
+      if (!(ptr < 0.f)) {
+        float pm = warp_max(fabsf(p));
+        return (pm <= kStepTol * amax) ? CS_ST_OK : CS_ST_NOPROGRESS;
+      }
+      float dfm;
+      float alpha = line_search(p, &dfm);
+      float dp = alpha * p;
+      add_to_a(dp);
+      *iters = k + 1;
+      float smax = warp_max(fabsf(dp));
+      prev_small = (smax <= kStepTol * amax) && (dfm <= kForceTol * fmax);
+      prev_bits = act_bits;
+    }
+  }
+
+  // ---------------------------------------------------------- adjoint
+  // Solve H w = g at the current point (Eq. 17) by iterative refinement with
+  // compensated residuals.  Leaves w in (wh, wl), lambda = D_act . J w in
+  // Lam() for every row < m.
+  __device__ __forceinline__ void adjoint(float& wh, float& wl) {
+    wh = chol_solve(gj);
+    wl = 0.f;
+    const float* Jm = Js();
+    float* Lm = Lam();
+    const int* idx = Idx();
+    float lam_prev[MT];
+#pragma unroll
+    for (int t = 0; t < MT; ++t) lam_prev[t] = 0.f;
+    float dmax_prev = CUDART_INF_F;
+    for (int it = 0; it <= kAdjointRefineMax; ++it) {
+      put_vec(V_WH, wh);
+      put_vec(V_WL, wl);
+      const float* vh = Vec(V_WH);
+      const float* vl = Vec(V_WL);
+      float s[MT], c[MT];
+#pragma unroll
+      for (int t = 0; t < MT; ++t) { s[t] = 0.f; c[t] = 0.f; }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        float xh = vh[k], xl = vl[k];
+#pragma unroll
+        for (int t = 0; t < MT; ++t)
+          if (32 * t < m) dot2(s[t], c[t], Jm[(lane + 32 * t) * G::JS + k], xh, xl);
+      }
+      float lmax = 0.f, dl = 0.f;
+#pragma unroll
+      for (int t = 0; t < MT; ++t) {
+        if (32 * t < m) {
+          bool on = (act_bits >> t) & 1u;
+          float lam = on ? D_r[t] * __fadd_rn(s[t], c[t]) : 0.f;
+          if (row_valid(t)) Lm[lane + 32 * t] = lam;
+          lmax = fmaxf(lmax, fabsf(lam));
+          dl = fmaxf(dl, fabsf(lam - lam_prev[t]));
+          lam_prev[t] = lam;
+        }
+      }
+      lmax = warp_max(lmax);
+      dl = warp_max(dl);
+      __syncwarp();
+      if (it > 0) {
+        float wmax = warp_max(fabsf(wh));
+        if ((dmax_prev <= kStepTol * wmax && dl <= kForceTol * lmax) ||
+            it == kAdjointRefineMax)
+          break;
+      }
+      // rho = g - M w - J^T lambda (compensated)
+      float ms = 0.f, mc = 0.f, js = 0.f, jc = 0.f;
+      if (lane < NV) {
+        const float* Mr = Ms() + lane * G::MS;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) dot2(ms, mc, Mr[k], vh[k], vl[k]);
+        for (int q = 0; q < nact; ++q) {
+          int i = idx[q];
+          dot2s(js, jc, Jm[i * G::JS + lane], Lm[i]);
+        }
+      }
+      float t1, e1, t2, e2;
+      two_sum(gj, -ms, t1, e1);
+      two_sum(t1, -js, t2, e2);
+      float rho = __fadd_rn(t2, __fsub_rn(__fadd_rn(e1, e2), __fadd_rn(mc, jc)));
+      if (lane >= NV) rho = 0.f;
+      float dw = chol_solve(rho);
+      dmax_prev = warp_max(fabsf(dw));
+      float s2, e3;
+      two_sum(wh, dw, s2, e3);
+      float lo = __fadd_rn(wl, e3);
+      wh = __fadd_rn(s2, lo);
+      wl = __fsub_rn(lo, __fsub_rn(wh, s2));
+    }
+    __syncwarp();
+  }
+
+  // Write dqfrc = w, daref = lambda, dJ = -(f w^T + lambda a^T).
+  __device__ __forceinline__ void write_grads(const Params& P, const cs_inst& e, float wh) {
+    if (lane < nv) P.dqfrc[e.off_v + lane] = wh;
+    const float* Lm = Lam();
+    const float* F = Fs();
+#pragma unroll
+    for (int t = 0; t < MT; ++t)
+      if (row_valid(t)) P.daref[e.off_r + lane + 32 * t] = Lm[lane + 32 * t];
+    put_vec(V_WH, wh);
+    put_vec(V_X, ah);
+    const float* vw = Vec(V_WH);
+    const float* va = Vec(V_X);
+    float* dJ = P.dJ + e.off_J;
+    const int mnv = m * nv;
+    for (int q = lane; q < mnv; q += 32) {
+      int rr, cc;
+      if (nv == NV) { rr = q / NV; cc = q - rr * NV; }
+      else { rr = q / nv; cc = q - rr * nv; }
+      dJ[q] = -__fmaf_rn(F[rr], vw[cc], Lm[rr] * va[cc]);
+    }
+  }
+
+  // Load the factor kept by the forward pass (packed lower rows of the real
+  // nv x nv block; padded rows are the identity).
+  __device__ __forceinline__ void load_factor(const float* Lp) {
+    float* L = Ls();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float v = 0.f;
+      if (lane < NV && k <= lane) {
+        if (lane < nv) v = __ldg(Lp + lane * (lane + 1) / 2 + k);
+        else v = (k == lane) ? 1.f : 0.f;
+      }
+      h[k] = v;
+    }
+    if (lane < NV) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) L[lane * G::MS + k] = h[k];
+    }
+    __syncwarp();
+    if (lane < NV) dinv = 1.0f / L[lane * G::MS + lane];
+  }
+
+  __device__ __forceinline__ void store_factor(float* Lp) {
+    if (lane < nv) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        if (k <= lane) Lp[lane * (lane + 1) / 2 + k] = h[k];
+    }
+  }
+
+  // ------------------------------------------------------------ drivers
+  template <int MODE>
+  __device__ __forceinline__ void run(const Params& P, int b) {
+    const cs_inst e = P.inst[b];
+    if (!load(P, e)) {
+      if (lane == 0) {
+        P.status[b] = CS_ST_BADSHAPE;
+        P.iters[b] = 0;
+      }
+      return;
+    }
+    if (MODE == MODE_FWD || MODE == MODE_FUSED) {
+      gj = (MODE == MODE_FUSED && lane < nv) ? __ldg(P.g + e.off_v + lane) : 0.f;
+      int iters = 0;
+      int st = forward(P, &iters);
+      if (lane < nv) P.a[e.off_v + lane] = ah;
+      if (lane == 0) {
+        P.status[b] = st;
+        P.iters[b] = iters;
+      }
+      if (st == CS_ST_CHOLFAIL || st == CS_ST_NONFINITE) {
+        if (MODE == MODE_FUSED) zero_grads(P, e);
+        return;
+      }
+      if (MODE == MODE_FWD) {
+        if (lane < nv) P.a_lo[e.off_v + lane] = al;
+#pragma unroll
+        for (int t = 0; t < MT; ++t)
+          if (row_valid(t)) P.act[e.off_r + lane + 32 * t] = (act_bits >> t) & 1u;
+        if (P.keep_factor && P.Lst) {
+          if (need_refactor())
+            if (!assemble_and_factor()) {
+              if (lane == 0) P.status[b] = CS_ST_CHOLFAIL;
+              return;
+            }
+          store_factor(P.Lst + e.off_M);
+        }
+        return;
+      }
+      // fused: adjoint at the returned point
+      if (need_refactor())
+        if (!assemble_and_factor()) {
+          if (lane == 0) P.status[b] = CS_ST_CHOLFAIL;
+          zero_grads(P, e);
+          return;
+        }
+      float wh, wl;
+      adjoint(wh, wl);
+      write_grads(P, e, wh);
+    } else {  // MODE_ADJ
+      gj = (lane < nv) ? __ldg(P.g + e.off_v + lane) : 0.f;
+      int st0 = P.status[b];
+      if (st0 == CS_ST_CHOLFAIL || st0 == CS_ST_NONFINITE || st0 == CS_ST_BADSHAPE) {
+        zero_grads(P, e);
+        return;
+      }
+      ah = (lane < nv) ? __ldg(P.a + e.off_v + lane) : 0.f;
+      al = (lane < nv) ? __ldg(P.a_lo + e.off_v + lane) : 0.f;
+      float scale;
+      bool bad;
+      residual(&scale, &bad);  // jar, f, active list at a*
+      uint32_t kept = 0;
+#pragma unroll
+      for (int t = 0; t < MT; ++t)
+        if (row_valid(t) && P.act[e.off_r + lane + 32 * t]) kept |= 1u << t;
+      if (P.keep_factor && P.Lst) {
+        load_factor(P.Lst + e.off_M);
+        fmask_bits = kept;
+        fmask_valid = true;
+      } else {
+        fmask_valid = false;
+      }
+      if (need_refactor())
+        if (!assemble_and_factor()) {
+          if (lane == 0) P.status[b] = CS_ST_CHOLFAIL;
+          zero_grads(P, e);
+          return;
+        }
+      float wh, wl;
+      adjoint(wh, wl);
+      write_grads(P, e, wh);
+    }
+  }
+
+  __device__ __forceinline__ void zero_grads(const Params& P, const cs_inst& e) {
+    if (lane < nv) P.dqfrc[e.off_v + lane] = 0.f;
+    for (int i = lane; i < m; i += 32) P.daref[e.off_r + i] = 0.f;
+    for (int q = lane; q < m * nv; q += 32) P.dJ[e.off_J + q] = 0.f;
+  }
+};
+
+// One warp per instance; warps claim instances dynamically (counter) or in a
+// static round-robin.
+template <int NV, int MT, int MODE>
+__global__ void __launch_bounds__(256) warp_solve_kernel(const __grid_constant__ Params P) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  using G = Geo<NV, MT>;
+  const int warp = threadIdx.x >> 5;
+  WarpSolver<NV, MT> S;
+  S.sm = reinterpret_cast<float*>(smem_raw + (size_t)warp * G::kBytes);
+  S.lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  int idx = blockIdx.x * wpb + warp;
+  const int stride = gridDim.x * wpb;
+  for (int guard = 0; guard <= P.n; ++guard) {
+    if (P.counter) {
+      int v = 0;
+      if (S.lane == 0) v = atomicAdd(P.counter, 1);
+      idx = __shfl_sync(kFull, v, 0);
+    }
+    if (idx >= P.n) break;
+    const int b = P.order ? P.order[idx] : idx;
+    if (b >= 0 && b < P.n) S.template run<MODE>(P, b);
+    __syncwarp();
+    if (!P.counter) idx += stride;
+  }
+}
+
+}  // namespace csk

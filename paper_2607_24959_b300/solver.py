@@ -1,0 +1,226 @@
+"""Python entry points over the C ABI (torch tensors in, torch tensors out).
+
+Names follow the C ABI: ``solve_fwd``, ``solve_adjoint``, ``solve_fused``.
+PyTorch only provides device memory and the current CUDA stream; every
+numerical step runs in ``libcs_b300.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _lib
+
+DEFAULT_TOL = 1e-8
+DEFAULT_MAX_ITER = 50
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclasses.dataclass
+class DeviceBatch:
+    """A packed ragged batch resident on one GPU (layout of cs_batch)."""
+
+    inst: torch.Tensor     # uint8 view of the cs_inst table (40 B / instance)
+    M: torch.Tensor
+    J: torch.Tensor
+    qfrc: torch.Tensor
+    aref: torch.Tensor
+    D: torch.Tensor
+    n: int
+    nv_max: int
+    m_max: int
+    inst_host: np.ndarray  # the same table on the host
+
+    @classmethod
+    def from_workload(cls, w, device="cuda"):
+        dev = torch.device(device)
+        f = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev)
+        inst = torch.from_numpy(np.ascontiguousarray(w.inst).view(np.uint8)).to(dev)
+        return cls(inst, f(w.M), f(w.J), f(w.qfrc), f(w.aref), f(w.D), w.n,
+                   max(w.nv_max, 1), w.m_max, np.ascontiguousarray(w.inst))
+
+    def with_data(self, M=None, J=None, qfrc=None, aref=None, D=None):
+        """Same layout, other data tensors (used by the autograd wrapper)."""
+        return dataclasses.replace(
+            self, M=self.M if M is None else M, J=self.J if J is None else J,
+            qfrc=self.qfrc if qfrc is None else qfrc,
+            aref=self.aref if aref is None else aref, D=self.D if D is None else D)
+
+    @property
+    def total_v(self):
+        return self.qfrc.numel()
+
+    @property
+    def total_r(self):
+        return self.aref.numel()
+
+    def cstruct(self) -> _lib.CsBatch:
+        for t in (self.M, self.J, self.qfrc, self.aref, self.D):
+            if t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+                raise ValueError("batch data must be contiguous float32 CUDA tensors")
+        b = _lib.CsBatch()
+        b.n = self.n
+        b.nv_max = self.nv_max
+        b.m_max = self.m_max
+        b.inst = self.inst.data_ptr()
+        b.M = self.M.data_ptr()
+        b.J = self.J.data_ptr() if self.J.numel() else self.M.data_ptr()
+        b.qfrc = self.qfrc.data_ptr()
+        b.aref = self.aref.data_ptr() if self.aref.numel() else self.qfrc.data_ptr()
+        b.D = self.D.data_ptr() if self.D.numel() else self.qfrc.data_ptr()
+        b.total_M = self.M.numel()
+        b.total_J = self.J.numel()
+        b.total_v = self.qfrc.numel()
+        b.total_r = self.aref.numel()
+        return b
+
+
+def options(tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER, keep_factor=True,
+            warps_per_block=0) -> _lib.CsOptions:
+    o = _lib.CsOptions()
+    o.tol = float(tol)
+    o.max_iter = int(max_iter)
+    o.keep_factor = 1 if keep_factor else 0
+    o.warps_per_block = int(warps_per_block)
+    return o
+
+
+@dataclasses.dataclass
+class State:
+    """Adjoint state of cs_solve_fwd (device tensors); size independent of K."""
+
+    a_lo: torch.Tensor
+    act: torch.Tensor
+    L: torch.Tensor | None
+    status: torch.Tensor
+    iters: torch.Tensor
+    keep_factor: bool
+
+    def cstruct(self) -> _lib.CsState:
+        s = _lib.CsState()
+        s.a_lo = self.a_lo.data_ptr()
+        s.act = self.act.data_ptr()
+        s.L = self.L.data_ptr() if self.L is not None else None
+        s.status = self.status.data_ptr()
+        s.iters = self.iters.data_ptr()
+        return s
+
+    def nbytes(self) -> int:
+        return sum(t.numel() * t.element_size()
+                   for t in (self.a_lo, self.act, self.L, self.status, self.iters)
+                   if t is not None)
+
+
+def alloc_state(batch: DeviceBatch, keep_factor=True) -> State:
+    dev = batch.M.device
+    return State(
+        a_lo=torch.empty(max(batch.total_v, 1), dtype=torch.float32, device=dev),
+        act=torch.empty(max(batch.total_r, 1), dtype=torch.uint8, device=dev),
+        L=(torch.empty(max(batch.M.numel(), 1), dtype=torch.float32, device=dev)
+           if keep_factor else None),
+        status=torch.empty(max(batch.n, 1), dtype=torch.int32, device=dev),
+        iters=torch.empty(max(batch.n, 1), dtype=torch.int32, device=dev),
+        keep_factor=bool(keep_factor))
+
+
+def solve_fwd(batch: DeviceBatch, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
+              keep_factor=True, warps_per_block=0, a=None, state=None):
+    """Forward solve; returns (a, state)."""
+    lib = _lib.load()
+    dev = batch.M.device
+    if a is None:
+        a = torch.empty(max(batch.total_v, 1), dtype=torch.float32, device=dev)
+    if state is None:
+        state = alloc_state(batch, keep_factor)
+    b = batch.cstruct()
+    o = options(tol, max_iter, keep_factor, warps_per_block)
+    st = state.cstruct()
+    _lib.check(lib.cs_solve_fwd(ctypes.byref(b), ctypes.byref(o), _ptr(a),
+                                ctypes.byref(st), _stream()), "cs_solve_fwd")
+    return a, state
+
+
+def solve_adjoint(batch: DeviceBatch, a, state: State, g, tol=DEFAULT_TOL,
+                  max_iter=DEFAULT_MAX_ITER, warps_per_block=0, out=None):
+    """IFT adjoint at the forward state; returns (dqfrc, daref, dJ)."""
+    lib = _lib.load()
+    dev = batch.M.device
+    if out is None:
+        out = (torch.empty(max(batch.total_v, 1), dtype=torch.float32, device=dev),
+               torch.empty(max(batch.total_r, 1), dtype=torch.float32, device=dev),
+               torch.empty(max(batch.J.numel(), 1), dtype=torch.float32, device=dev))
+    dq, dr, dJ = out
+    b = batch.cstruct()
+    o = options(tol, max_iter, state.keep_factor, warps_per_block)
+    st = state.cstruct()
+    g = g.contiguous()
+    _lib.check(lib.cs_solve_adjoint(ctypes.byref(b), ctypes.byref(o), _ptr(a),
+                                    ctypes.byref(st), _ptr(g), _ptr(dq), _ptr(dr),
+                                    _ptr(dJ), _stream()), "cs_solve_adjoint")
+    return dq, dr, dJ
+
+
+def fused_workspace_bytes(n: int) -> int:
+    return int(_lib.load().cs_fused_workspace_bytes(int(n)))
+
+
+@dataclasses.dataclass
+class FusedOut:
+    a: torch.Tensor
+    dqfrc: torch.Tensor
+    daref: torch.Tensor
+    dJ: torch.Tensor
+    status: torch.Tensor
+    iters: torch.Tensor
+    workspace: torch.Tensor
+
+
+def alloc_fused(batch: DeviceBatch) -> FusedOut:
+    dev = batch.M.device
+    ws = torch.zeros(fused_workspace_bytes(batch.n), dtype=torch.uint8, device=dev)
+    return FusedOut(
+        a=torch.empty(max(batch.total_v, 1), dtype=torch.float32, device=dev),
+        dqfrc=torch.empty(max(batch.total_v, 1), dtype=torch.float32, device=dev),
+        daref=torch.empty(max(batch.total_r, 1), dtype=torch.float32, device=dev),
+        dJ=torch.empty(max(batch.J.numel(), 1), dtype=torch.float32, device=dev),
+        status=torch.empty(max(batch.n, 1), dtype=torch.int32, device=dev),
+        iters=torch.empty(max(batch.n, 1), dtype=torch.int32, device=dev),
+        workspace=ws)
+
+
+def solve_fused(batch: DeviceBatch, g, order=None, tol=DEFAULT_TOL,
+                max_iter=DEFAULT_MAX_ITER, warps_per_block=0, out: FusedOut | None = None):
+    """Fused forward + adjoint in one persistent launch; returns FusedOut."""
+    lib = _lib.load()
+    if out is None:
+        out = alloc_fused(batch)
+    b = batch.cstruct()
+    o = options(tol, max_iter, True, warps_per_block)
+    g = g.contiguous()
+    _lib.check(lib.cs_solve_fused(
+        ctypes.byref(b), ctypes.byref(o), _ptr(g), _ptr(order), _ptr(out.a),
+        _ptr(out.dqfrc), _ptr(out.daref), _ptr(out.dJ), _ptr(out.status),
+        _ptr(out.iters), _ptr(out.workspace), out.workspace.numel(), _stream()),
+        "cs_solve_fused")
+    return out
+
+
+def cost_order(inst_host: np.ndarray) -> np.ndarray:
+    """Claim order for the persistent kernel: most expensive instances first.
+
+    Cost model per instance: m*nv^2 + nv^3 (the Newton-matrix assembly and the
+    Cholesky factor dominate an iteration)."""
+    nv = inst_host["nv"].astype(np.int64)
+    m = inst_host["m"].astype(np.int64)
+    cost = m * nv * nv + nv ** 3
+    return np.argsort(-cost, kind="stable").astype(np.int32)

@@ -1,0 +1,105 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path, run the oracle on
+the same seeded inputs, compare instance by instance.
+
+Tolerances (per instance, per output array, relative to the oracle's
+infinity norm):  a <= 1e-4;  dqfrc, daref, dJ <= 1e-3;  active sets
+bit-identical on non-degenerate instances.  An instance is degenerate when a
+row sits on the cone boundary at the oracle's solution:
+|jar_i| < DEG_MARGIN * (sum_k |J_ik a_k| + |aref_i|); there the active set and
+the adjoint are not defined (the derivative is local to a fixed contact set).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+
+A_TOL = 1e-4
+G_TOL = 1e-3
+DEG_MARGIN = 1e-6
+
+
+def rel(x, y):
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    if y.size == 0:
+        return 0.0
+    d = np.max(np.abs(x - y))
+    return float(d / max(np.max(np.abs(y)), 1e-30))
+
+
+def run_gpu_fused(batch, w, **kw):
+    from paper_2607_24959_b300 import solver
+    g = torch.from_numpy(np.ascontiguousarray(w.g, np.float32)).to(batch.M.device)
+    out = solver.solve_fused(batch, g, **kw)
+    torch.cuda.synchronize()
+    return dict(a=out.a.cpu().numpy(), dqfrc=out.dqfrc.cpu().numpy(),
+                daref=out.daref.cpu().numpy(), dJ=out.dJ.cpu().numpy(),
+                status=out.status.cpu().numpy(), iters=out.iters.cpu().numpy())
+
+
+def run_gpu_split(batch, w, keep_factor=True, **kw):
+    from paper_2607_24959_b300 import solver
+    g = torch.from_numpy(np.ascontiguousarray(w.g, np.float32)).to(batch.M.device)
+    a, st = solver.solve_fwd(batch, keep_factor=keep_factor, **kw)
+    dq, dr, dJ = solver.solve_adjoint(batch, a, st, g, **kw)
+    torch.cuda.synchronize()
+    return dict(a=a.cpu().numpy(), dqfrc=dq.cpu().numpy(), daref=dr.cpu().numpy(),
+                dJ=dJ.cpu().numpy(), status=st.status.cpu().numpy(),
+                iters=st.iters.cpu().numpy(), act=st.act.cpu().numpy(),
+                a_lo=st.a_lo.cpu().numpy())
+
+
+def compare(w, gpu, ref, idx, check_act=True):
+    """Per-instance comparison; returns a summary dict (fails nothing)."""
+    worst = dict(a=0.0, dqfrc=0.0, daref=0.0, dJ=0.0)
+    bad = []
+    degenerate = 0
+    act_mismatch = []
+    for b in idx:
+        e = w.inst[b]
+        nv, m = int(e["nv"]), int(e["m"])
+        ov, orr, oJ = int(e["off_v"]), int(e["off_r"]), int(e["off_J"])
+        if ref["status"][b] != 0:
+            continue
+        p = w.instance(b)
+        a_ref = ref["a"][ov:ov + nv]
+        jar = p["J"].astype(np.float64) @ a_ref - p["aref"]
+        scale = np.abs(p["J"].astype(np.float64)) @ np.abs(a_ref) + np.abs(p["aref"])
+        deg = bool(m) and bool(np.any(np.abs(jar) < DEG_MARGIN * scale))
+        if deg:
+            # a* is continuous across the boundary, so it is still checked
+            degenerate += 1
+            ea = rel(gpu["a"][ov:ov + nv], a_ref)
+            worst["a"] = max(worst["a"], ea)
+            if ea > A_TOL or gpu["status"][b] != 0:
+                bad.append((int(b), dict(a=ea), int(gpu["status"][b]),
+                            int(gpu["iters"][b])))
+            continue
+        errs = dict(
+            a=rel(gpu["a"][ov:ov + nv], a_ref),
+            dqfrc=rel(gpu["dqfrc"][ov:ov + nv], ref["dqfrc"][ov:ov + nv]),
+            daref=rel(gpu["daref"][orr:orr + m], ref["daref"][orr:orr + m]) if m else 0.0,
+            dJ=rel(gpu["dJ"][oJ:oJ + m * nv], ref["dJ"][oJ:oJ + m * nv]) if m else 0.0,
+        )
+        for k, v in errs.items():
+            worst[k] = max(worst[k], v)
+        ok = (errs["a"] <= A_TOL and errs["dqfrc"] <= G_TOL and errs["daref"] <= G_TOL
+              and errs["dJ"] <= G_TOL and gpu["status"][b] == 0)
+        if check_act and m:
+            act_ref = ref["act"][orr:orr + m].astype(bool)
+            if "act" in gpu:
+                act_gpu = gpu["act"][orr:orr + m].astype(bool)
+            else:
+                act_gpu = gpu["daref"][orr:orr + m] != 0
+                # daref is zero exactly on inactive rows; an active row with
+                # J w = 0 exactly would read as inactive, which random data
+                # never produces.
+            if not np.array_equal(act_gpu, act_ref):
+                act_mismatch.append(int(b))
+                ok = False
+        if not ok:
+            bad.append((int(b), errs, int(gpu["status"][b]), int(gpu["iters"][b])))
+    return dict(worst=worst, bad=bad, degenerate=degenerate, act_mismatch=act_mismatch,
+                checked=len(idx))
