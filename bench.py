@@ -1,0 +1,384 @@
+"""Benchmark: fused forward + IFT-adjoint contact solves per second.
+
+Default workload: the quadruped horizon batch -- 512 trajectories x 64 steps =
+32768 independent solves, nv = 18, contacts per instance uniform in 0..32
+(4 pyramid rows each, so m in 0..128), FP32 on the GPU.  One step = one pass
+of the whole hot path (stage, Newton solve with exact line search, IFT adjoint,
+write a, dL/dqfrc, dL/daref, dL/dJ) over the batch, launched as one
+CUDA-graph replay of the persistent fused kernel.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample instead (the reference arm of this benchmark).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+IFT-adjoint contact solves/s at nv=18,nc=32; serve p50/p99 latency"
+UNIT = "solves/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0, period_ms=200):
+        self.index = index
+        self.period_ms = period_ms
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", f"-lms={self.period_ms}"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_work(inst, iters, act_counts):
+    """Algorithmic FLOPs and bytes of one fused launch (per-instance sums).
+
+    FLOPs: a0 = nv^3/3 + 2nv^2; per Newton iteration 4 m nv (J a, J^T f) +
+    2 nv^2 (M a) + m_act nv (nv+1) (H) + nv^3/3 + 2 nv^2 (factor + solves) +
+    2 m nv + 8 m (line search); the adjoint 2 nv^2 + 4 m nv; m_act is the
+    final active count.  Bytes (4 B each): read M lower (nv(nv+1)/2), J (m nv),
+    qfrc, g (2 nv), aref, D (2 m); write a, dqfrc (2 nv), daref (m), dJ (m nv).
+    Work the algorithm does not need (padding, inactive rows in H, the
+    compensated-arithmetic overhead, extra refinement passes) is not counted.
+    """
+    nv = inst["nv"].astype(np.float64)
+    m = inst["m"].astype(np.float64)
+    k = iters.astype(np.float64)
+    ma = act_counts.astype(np.float64)
+    per_it = 4 * m * nv + 2 * nv ** 2 + ma * nv * (nv + 1) + nv ** 3 / 3 + 2 * nv ** 2 \
+        + 2 * m * nv + 8 * m
+    flops = nv ** 3 / 3 + 2 * nv ** 2 + k * per_it + 2 * nv ** 2 + 4 * m * nv
+    byts = 4 * (nv * (nv + 1) / 2 + m * nv + 2 * nv + 2 * m + 2 * nv + m + m * nv)
+    return float(flops.sum()), float(byts.sum())
+
+
+def make_workload(name, rank, n=None):
+    from paper_2607_24959_b300 import workloads as W
+    seed_shift = 7919 * rank
+    kw = {} if n is None else {"n": n}
+    if name == "quadruped":
+        return W.quadruped(seed=W.SEEDS["quadruped"] + seed_shift, **kw)
+    if name == "franka":
+        return W.franka(seed=W.SEEDS["franka"] + seed_shift, **kw)
+    if name == "tiny":
+        return W.tiny(seed=W.SEEDS["tiny"] + seed_shift, **kw)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(name, w):
+    p = w.params
+    return {"workload": f"{name}: {w.n} solves, nv={p['nv']}, m=4*nc, "
+                        f"nc~U{{0..{w.m_max // 4}}}" if name == "quadruped" else
+            f"{name}: {w.n} solves, nv={p['nv']}, m={w.m_max}",
+            "instances": w.n, "nv": p["nv"], "m_max": w.m_max,
+            "mean_m": float(w.inst["m"].mean()), "cond_M": p["cond"],
+            "D_range": list(p["d_range"]), "seed": p["seed"]}
+
+
+def cpu_baseline(w, max_instances=None, threads=None):
+    """The FP64 oracle, as it stands, on the host cores."""
+    import oracle
+    threads = threads or (os.cpu_count() or 1)
+    n = w.n if max_instances is None else min(w.n, max_instances)
+    ws = w if n == w.n else w.subset(np.arange(n))
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.solve_workload(ws, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n} of the {w.n} instances, forward + adjoint, "
+                      f"{threads} threads, {dt:.2f} s wall"}
+
+
+def run_reference(args):
+    ws_, rank = _dist()
+    if rank != 0:
+        return
+    w = make_workload(args.workload, 0, args.n)
+    n_sample = args.ref_sample
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(w, max_instances=min(256, n_sample))
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, max_instances=n_sample))
+    v = statistics.median([x["value"] for x in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * n_sample / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.workload, w),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"],
+                             "kind": "oracle", "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2607_24959_b300 import solver, _lib
+
+    world, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _lib.load()
+    w = make_workload(args.workload, rank, args.n)
+    batch = solver.DeviceBatch.from_workload(w, dev)
+    g = torch.from_numpy(w.g).to(dev)
+    order = torch.from_numpy(solver.cost_order(w.inst)).to(dev)
+    out = solver.alloc_fused(batch)
+    kw = dict(order=order, tol=args.tol, max_iter=args.max_iter,
+              warps_per_block=args.warps_per_block)
+
+    # plan: per-(nv, m) bucket kernels, cost-ordered claims, autotuned
+    # warps per block, captured as one CUDA graph (tuning runs happen here)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        plan = solver.FusedPlan(batch, g, tol=args.tol, max_iter=args.max_iter,
+                                autotune=args.warps_per_block == 0, graph=True,
+                                warps_per_block=args.warps_per_block, out=out)
+        for _ in range(args.warmup):
+            plan.launch()
+    torch.cuda.synchronize()
+    plan_info = plan.describe()
+
+    # ---- timed region: K graph replays on `stream`
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(index=local) as clk:
+        barrier()
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(args.steps):
+                plan.launch()
+            ev1.record(stream)
+        barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    total_solves = w.n * world * args.steps
+    value = total_solves / (ms_total / 1e3)
+
+    status = out.status.cpu().numpy()[:w.n]
+    iters = out.iters.cpu().numpy()[:w.n]
+    daref = out.daref.cpu().numpy()
+    act_counts = np.array([np.count_nonzero(daref[o:o + mm]) for o, mm in
+                           zip(w.inst["off_r"], w.inst["m"])])
+    flops, byts = algorithmic_work(w.inst, iters, act_counts)
+    peaks, peak_src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12  # TFLOP/s
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    t_s = ms_step / 1e3
+    tflops = flops / t_s / 1e12
+    gbs = byts / t_s / 1e9
+    frac_alu = tflops / fp32_peak
+    frac_hbm = gbs / hbm_peak
+    if frac_alu >= frac_hbm:
+        roof = {"bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": frac_alu, "traffic": None,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x "
+                               f"{peaks.get('sm_max_mhz', 2032.0)} MHz ({peak_src} clock)",
+                "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": frac_hbm, "peak_source": f"{peak_src} hbm_gbs"}}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": frac_hbm, "traffic": None}
+    roof["kernel"] = "warp_solve_kernel<NV,MT,FUSED> buckets (all launches of one step)"
+    roof["algorithmic_flops_per_launch"] = flops
+    roof["algorithmic_bytes_per_launch"] = byts
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, w, batch, dev, kw, world)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(args.workload, w),
+                           l2="inputs+outputs 330 MB per step exceed the 126 MB L2; no flush",
+                           graph="one CUDA-graph replay per step (plan)",
+                           claim_order="per bucket, cost-descending, dynamic counter"),
+            "roofline": roof, "clocks": clk.summary(),
+            "gpu_launches": args.steps * plan_info["kernels"], "plan": plan_info,
+            "status_counts": np.bincount(status, minlength=6).tolist(),
+            "iters_mean": float(iters.mean()), "iters_max": int(iters.max())}
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, max_instances=args.cpu_sample)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, w, batch, dev, kw, world):
+    """Same metric through the public API with pinned host buffers: every step
+    copies its inputs host->device, solves, and copies the results back."""
+    import torch
+    from paper_2607_24959_b300 import solver
+
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    h_in = dict(inst=pin(np.ascontiguousarray(w.inst).view(np.uint8)), M=pin(w.M), J=pin(w.J),
+                qfrc=pin(w.qfrc), aref=pin(w.aref), D=pin(w.D), g=pin(w.g))
+    d_in = {k: torch.empty_like(v, device=dev) for k, v in h_in.items()}
+    b2 = solver.DeviceBatch(d_in["inst"], d_in["M"], d_in["J"], d_in["qfrc"], d_in["aref"],
+                            d_in["D"], w.n, batch.nv_max, batch.m_max, batch.inst_host)
+    out = solver.alloc_fused(b2)
+    # a plan bound to the device-side staging buffers (tuned geometry is
+    # taken from the autotuner cache filled by the device-resident run)
+    plan = solver.FusedPlan(b2, d_in["g"], tol=args.tol, max_iter=args.max_iter,
+                            autotune=False, graph=True,
+                            warps_per_block=args.warps_per_block, out=out)
+    h_out = dict(a=torch.empty_like(out.a, device="cpu").pin_memory(),
+                 dqfrc=torch.empty_like(out.dqfrc, device="cpu").pin_memory(),
+                 daref=torch.empty_like(out.daref, device="cpu").pin_memory(),
+                 dJ=torch.empty_like(out.dJ, device="cpu").pin_memory(),
+                 status=torch.empty_like(out.status, device="cpu").pin_memory())
+    h2d = sum(v.numel() * v.element_size() for v in h_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values())
+    def step():
+        for k in d_in:
+            d_in[k].copy_(h_in[k], non_blocking=True)
+        plan.launch()
+        h_out["a"].copy_(out.a, non_blocking=True)
+        h_out["dqfrc"].copy_(out.dqfrc, non_blocking=True)
+        h_out["daref"].copy_(out.daref, non_blocking=True)
+        h_out["dJ"].copy_(out.dJ, non_blocking=True)
+        h_out["status"].copy_(out.status, non_blocking=True)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    plan.close()
+    return {"value": w.n * world * args.steps / (ms / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": ms / args.steps}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="quadruped")
+    ap.add_argument("--n", type=int, default=None,
+                    help="instances (default: the workload's full size)")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--max-iter", type=int, default=50)
+    ap.add_argument("--warps-per-block", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=32768)
+    ap.add_argument("--ref-sample", type=int, default=4096)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

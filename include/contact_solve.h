@@ -158,6 +158,60 @@ int cs_solve_fused(const cs_batch* batch, const cs_options* opt,
                    int32_t* iters, void* workspace, size_t workspace_bytes,
                    void* stream);
 
+/* ---- execution plans (fused path) ------------------------------------- */
+
+/* Plan flags. */
+#define CS_PLAN_AUTOTUNE 1 /* time warps-per-block candidates per bucket */
+#define CS_PLAN_GRAPH 2    /* capture the launch as one CUDA graph */
+
+typedef struct cs_plan cs_plan; /* opaque, owned by the library */
+
+/* What a plan launches. */
+typedef struct cs_plan_info {
+  int32_t n_kernels;          /* one kernel per (nv bucket, rows per lane) */
+  int32_t graph;              /* 1 if launched as a CUDA graph */
+  int32_t nv_bucket[8];
+  int32_t rows_per_lane[8];   /* m <= 32 * rows_per_lane */
+  int32_t instances[8];
+  int32_t warps_per_block[8];
+  float tuned_ms[8];          /* autotuned time of the bucket alone (0 if not) */
+} cs_plan_info;
+
+/* Make a plan for the fused forward + adjoint (the work of cs_solve_fused)
+ * on one batch and one set of output buffers, all of which must outlive the
+ * plan.  inst_host is a host copy of batch->inst (read during the call only)
+ * used to bucket instances by (nv, m) and to order each bucket's claims by
+ * decreasing cost.  flags: CS_PLAN_AUTOTUNE times warps-per-block candidates
+ * on this data (this runs the solve; outputs are overwritten) unless
+ * opt->warps_per_block is set; CS_PLAN_GRAPH captures the bucket kernels as
+ * parallel branches of one CUDA graph.  The plan allocates its own device
+ * buffers (claim orders and counters).  Synchronises `stream` once.
+ * Returns CS_EINVAL, CS_ENOMEM, CS_ECUDA or CS_EUNSUPPORTED on failure (then
+ * *out is NULL). */
+int cs_plan_create_fused(const cs_batch* batch, const cs_options* opt,
+                         const cs_inst* inst_host, const float* g, float* a,
+                         float* dqfrc, float* daref, float* dJ, int32_t* status,
+                         int32_t* iters, int32_t flags, void* stream,
+                         cs_plan** out);
+
+/* Enqueue the plan's work on `stream` (one graph launch, or the bucket
+ * kernels in order).  Launches of one plan on different streams must not
+ * overlap in time: they share the claim counters. */
+int cs_plan_launch(cs_plan* plan, void* stream);
+
+/* Describe the plan's kernels. */
+int cs_plan_describe(const cs_plan* plan, cs_plan_info* info);
+
+/* Free the plan (after its last launch has completed). */
+void cs_plan_destroy(cs_plan* plan);
+
+/* Autotuner cache, one line per (device, nv bucket, rows per lane):
+ * "device nv_bucket rows_per_lane warps_per_block ms".  dump writes at most
+ * len-1 characters (NUL-terminated) and returns the full length; load parses
+ * such text and returns the number of entries taken. */
+int cs_autotune_cache_dump(char* buf, size_t len);
+int cs_autotune_cache_load(const char* text);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,16 @@ class CsState(ctypes.Structure):
                 ("status", c_void_p), ("iters", c_void_p)]
 
 
+class CsPlanInfo(ctypes.Structure):
+    _fields_ = [("n_kernels", c_int32), ("graph", c_int32),
+                ("nv_bucket", c_int32 * 8), ("rows_per_lane", c_int32 * 8),
+                ("instances", c_int32 * 8), ("warps_per_block", c_int32 * 8),
+                ("tuned_ms", c_float * 8)]
+
+
+CS_PLAN_AUTOTUNE = 1
+CS_PLAN_GRAPH = 2
+
 # name -> (restype, argtypes)
 _SIGS = {
     "cs_version": (ctypes.c_int, []),
@@ -66,6 +76,15 @@ _SIGS = {
                                       c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
                                       c_void_p]),
+    "cs_plan_create_fused": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
+                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, c_void_p, c_int32, c_void_p,
+                                            ctypes.POINTER(c_void_p)]),
+    "cs_plan_launch": (ctypes.c_int, [c_void_p, c_void_p]),
+    "cs_plan_describe": (ctypes.c_int, [c_void_p, ctypes.POINTER(CsPlanInfo)]),
+    "cs_plan_destroy": (None, [c_void_p]),
+    "cs_autotune_cache_dump": (ctypes.c_int, [ctypes.c_char_p, c_size_t]),
+    "cs_autotune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
 }
 
 _lock = threading.Lock()

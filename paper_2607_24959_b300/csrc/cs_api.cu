@@ -109,6 +109,7 @@ csk::Params make_params(const cs_batch* b, const cs_options* o) {
   csk::Params P;
   memset(&P, 0, sizeof(P));
   P.n = b->n;
+  P.n_work = b->n;
   P.inst = b->inst;
   P.M = b->M;
   P.J = b->J;

@@ -20,13 +20,18 @@ static cudaError_t launch_t(const csk::Params& P, const LaunchCfg& cfg, cudaStre
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // all of the unified L1/shared array as shared memory: the warps' slices
+  // are the working set, and occupancy is what hides the solver's latency
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < per_sm) per_sm = cfg.blocks_per_sm;
   long long grid = (long long)per_sm * device_sm_count();
-  const long long need = ((long long)P.n + wpb - 1) / wpb;
+  const long long need = ((long long)P.n_work + wpb - 1) / wpb;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   if (info) {

@@ -1,23 +1,29 @@
 // cs_warp.cuh -- one-warp-per-instance contact solver (device code).
 //
-// A warp owns one instance at a time.  Its M, J and D sit in the warp's slice
-// of shared memory; every per-row quantity (jar, J p, D, aref) is spread over
-// the lanes as "row i = lane + 32 t, t < MT"; every nv-vector is spread as
-// "element j on lane j" and broadcast through a small shared buffer.
+// A warp owns one instance at a time.  Its M, J, D and the Newton matrix /
+// Cholesky factor sit in the warp's slice of shared memory; every per-row
+// quantity (jar, J p, D, aref) is spread over the lanes as "row i = lane + 32
+// t, t < MT"; every nv-vector is spread as "element j on lane j" and broadcast
+// through a small shared buffer.
 //
 // Arithmetic (Section III of the paper):
 //  * residual r = M a - qfrc + J^T f, f = D . min(J a - aref, 0) (Eqs. 6, 8).
 //    a is carried as an unevaluated float pair (hi + lo) and r, jar are
 //    accumulated with error-free transformations (TwoSum / TwoProd), so the
 //    contact forces f keep their accuracy when a stiff row has |jar| << |J a|;
-//  * H = M + sum_{i active} D_i J_i^T J_i (Eq. 9), a warp Cholesky in
-//    registers (lane j holds row j), triangular solves by shuffles;
+//  * H = M + sum_{i active} D_i J_i^T J_i (Eq. 9), a left-looking Cholesky in
+//    shared memory (lane j computes row j), triangular solves by shuffles;
 //  * p = -H^-1 r and an exact line search on the piecewise-linear derivative
 //    of phi(alpha) = L(a + alpha p) (Eq. 10): safeguarded Newton on phi' that
 //    stops when no breakpoint separates the trial point from its Newton
 //    point, which makes the returned alpha the exact root;
 //  * the IFT adjoint H w = g (Eq. 17), refined with compensated residuals so
 //    that D_act . (J w) keeps its accuracy for stiff rows.
+//
+// Code size matters as much as instruction count here: a fully unrolled
+// solver overflows the instruction cache (measured: "no instruction" was the
+// dominant stall), so loops over nv and over rows stay rolled and only the
+// short per-lane row loops (t < MT) are unrolled.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -63,6 +69,13 @@ __device__ __forceinline__ void dot2s(float& s, float& c, float x, float y) {
   s = t;
   c = __fadd_rn(c, __fadd_rn(te, pe));
 }
+// (s, c) += (s2, c2) for unnormalised float pairs.
+__device__ __forceinline__ void add_pair(float& s, float& c, float s2, float c2) {
+  float t, e;
+  two_sum(s, s2, t, e);
+  s = t;
+  c = __fadd_rn(__fadd_rn(c, c2), e);
+}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -94,17 +107,18 @@ struct Geo {
   static constexpr int oF = oD + MCAP;               // f   MCAP
   static constexpr int oLam = oF + MCAP;             // lambda = D_act J w
   static constexpr int oIdx = oLam + MCAP;           // active rows (int)
-  static constexpr int oVec = oIdx + MCAP;           // 6 broadcast vectors
-  static constexpr int kVec = 6;
+  static constexpr int oVec = oIdx + MCAP;           // broadcast vectors
+  static constexpr int kVec = 7;
   static constexpr int kWords = oVec + kVec * 32;
   static constexpr int kBytes = ((kWords * 4) + 127) & ~127;
 };
 
-enum VecSlot { V_AH = 0, V_AL = 1, V_P = 2, V_WH = 3, V_WL = 4, V_X = 5 };
+enum VecSlot { V_AH = 0, V_AL = 1, V_P = 2, V_WH = 3, V_WL = 4, V_X = 5, V_DINV = 6 };
 
 // Kernel parameters (one struct, passed by value).
 struct Params {
-  int32_t n;
+  int32_t n;                // instances in the batch (bound for indices)
+  int32_t n_work;           // claimable entries (order length, or n)
   const cs_inst* inst;
   const float *M, *J, *qfrc, *aref, *D, *g;
   int64_t total_M, total_J, total_v, total_r;
@@ -134,15 +148,13 @@ struct WarpSolver {
   // row registers: row i = lane + 32 t
   float aref_r[MT], D_r[MT], jar_r[MT], s_r[MT];
   uint32_t act_bits;    // bit t: row lane+32t active at the current point
-  uint32_t fmask_bits;  // active set the factor in h[] belongs to
+  uint32_t fmask_bits;  // active set the factor in Ls() belongs to
   bool fmask_valid;
   int nact;
   // element registers (lane j < NV)
   float ah, al;          // a = ah + al
   float qf, gj;          // qfrc_j, g_j
   float r, maq;          // r_j, (M a - qfrc)_j
-  float h[NV];           // row j of the current Cholesky factor
-  float dinv;            // 1 / L_jj
   float fmax;            // max |f| at the current point
   float qmax;            // max |qfrc|
 
@@ -179,37 +191,34 @@ struct WarpSolver {
     const float* J = P.J + e.off_J;
     float* Ms_ = Ms();
     float* Js_ = Js();
+#pragma unroll 1
     for (int q = lane; q < NV * NV; q += 32) {
       int rr = q / NV, cc = q - rr * NV;
       float v = (rr < nv && cc < nv) ? __ldg(M + rr * nv + cc) : (rr == cc ? 1.f : 0.f);
       Ms_[rr * G::MS + cc] = v;
     }
     const int mnv = m * nv;
-    if (nv == NV) {
-      if ((reinterpret_cast<uintptr_t>(J) & 15) == 0) {
-        const float4* J4 = reinterpret_cast<const float4*>(J);
-        for (int q = lane; q < (mnv >> 2); q += 32) {
-          float4 v = __ldg(J4 + q);
-          int b = 4 * q;
-          int rr = b / NV, cc = b - rr * NV;
-          float vv[4] = {v.x, v.y, v.z, v.w};
+    if (nv == NV && (reinterpret_cast<uintptr_t>(J) & 15) == 0) {
+      const float4* J4 = reinterpret_cast<const float4*>(J);
+#pragma unroll 1
+      for (int q = lane; q < (mnv >> 2); q += 32) {
+        float4 v = __ldg(J4 + q);
+        int b = 4 * q;
+        int rr = b / NV, cc = b - rr * NV;
+        float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            Js_[rr * G::JS + cc] = vv[u];
-            if (++cc == NV) { cc = 0; ++rr; }
-          }
-        }
-        for (int q = (mnv & ~3) + lane; q < mnv; q += 32) {
-          int rr = q / NV, cc = q - rr * NV;
-          Js_[rr * G::JS + cc] = __ldg(J + q);
-        }
-      } else {
-        for (int q = lane; q < mnv; q += 32) {
-          int rr = q / NV, cc = q - rr * NV;
-          Js_[rr * G::JS + cc] = __ldg(J + q);
+        for (int u = 0; u < 4; ++u) {
+          Js_[rr * G::JS + cc] = vv[u];
+          if (++cc == NV) { cc = 0; ++rr; }
         }
       }
+#pragma unroll 1
+      for (int q = (mnv & ~3) + lane; q < mnv; q += 32) {
+        int rr = q / NV, cc = q - rr * NV;
+        Js_[rr * G::JS + cc] = __ldg(J + q);
+      }
     } else {
+#pragma unroll 1
       for (int q = lane; q < mnv; q += 32) {
         int rr = q / nv, cc = q - rr * nv;
         Js_[rr * G::JS + cc] = __ldg(J + q);
@@ -219,10 +228,12 @@ struct WarpSolver {
     // multiple of 32 (read by the row loops but never active)
     const int mpad = min(G::MCAP, (m + 31) & ~31);
     const int padc = G::JS - nv;
+#pragma unroll 1
     for (int q = lane; q < m * padc; q += 32) {
       int rr = q / padc, cc = nv + (q - rr * padc);
       Js_[rr * G::JS + cc] = 0.f;
     }
+#pragma unroll 1
     for (int q = m * G::JS + lane; q < mpad * G::JS; q += 32) Js_[q] = 0.f;
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
@@ -239,60 +250,61 @@ struct WarpSolver {
   }
 
   // ------------------------------------------------------------- Cholesky
-  // Factor the matrix whose lower rows are in Ls() (row stride MS).  Lane j
-  // keeps row j of L in h[]; L is also written back to Ls() for the
-  // transposed solve.  Returns false on a non-positive pivot.
-  //
-  // Every update below is branch-free with a compile-time index: a predicated
-  // form such as "if (lane >= jj) h[jj] = ..." lets the compiler re-roll the
-  // unrolled loop into one over a lane-dependent bound, which moves h[] to
-  // local memory.  Entries above the diagonal (k > lane) hold don't-care
-  // values and are never read into the lower triangle.
-  __device__ __forceinline__ bool factor_from_Ls() {
+  // Left-looking Cholesky of the lower rows in Ls(), in place.  At step k
+  // every lane j computes L[j][k] = H[j][k] - sum_{i<k} L[j][i] L[k][i]
+  // (equal trip counts, no divergence); lane k's value is the pivot.  The
+  // reciprocal pivots go to the V_DINV slot.  Returns false on a non-positive
+  // pivot.  The fp32 factor is only the preconditioner of a compensated
+  // iteration, so the reciprocal square root is the MUFU one.
+  __device__ __forceinline__ bool factor() {
     float* L = Ls();
-    {
-      const float* Lr = L + min(lane, NV - 1) * G::MS;
-#pragma unroll
-      for (int k = 0; k < NV; ++k) h[k] = Lr[k];
-    }
+    float* dv = Vec(V_DINV);
+    const float* Lj = L + min(lane, NV - 1) * G::MS;
     bool ok = true;
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < NV; ++k) {
-      float d = __shfl_sync(kFull, h[k], k);
-      ok = ok && (d > 0.f) && (d < CUDART_INF_F);
-      float sq = sqrtf(d);
-      float inv = 1.0f / sq;
-      dinv = (lane == k) ? inv : dinv;
-      h[k] = (lane == k) ? sq : h[k] * inv;
-#pragma unroll
-      for (int jj = k + 1; jj < NV; ++jj) {
-        float l = __shfl_sync(kFull, h[k], jj);
-        float lm = (lane >= jj) ? l : 0.f;
-        h[jj] = __fmaf_rn(-h[k], lm, h[jj]);
+      const float* Lk = L + k * G::MS;
+      float acc = Lj[k], acc2 = 0.f;
+      int i = 0;
+#pragma unroll 1
+      for (; i + 1 < k; i += 2) {
+        acc = __fmaf_rn(-Lj[i], Lk[i], acc);
+        acc2 = __fmaf_rn(-Lj[i + 1], Lk[i + 1], acc2);
       }
+      if (i < k) acc = __fmaf_rn(-Lj[i], Lk[i], acc);
+      acc += acc2;
+      const float d = __shfl_sync(kFull, acc, k);
+      ok = ok && (d > 0.f) && (d < CUDART_INF_F);
+      const float rs = rsqrtf(d);
+      __syncwarp();
+      if (lane == k) {
+        // the reciprocal pivot is derived from the stored diagonal, exactly as
+        // load_factor() does, so a kept factor solves bit-identically
+        const float lkk = d * rs;
+        L[k * G::MS + k] = lkk;
+        dv[k] = 1.0f / lkk;
+      } else if (lane > k && lane < NV) {
+        L[lane * G::MS + k] = acc * rs;
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    if (lane < NV) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) L[lane * G::MS + k] = h[k];
-    }
-    __syncwarp();
     return ok;
   }
 
   // z = (L L^T)^-1 x, vectors spread one element per lane.
   __device__ __forceinline__ float chol_solve(float x) {
     const float* L = Ls();
-#pragma unroll
+    const float* dv = Vec(V_DINV);
+#pragma unroll 1
     for (int k = 0; k < NV; ++k) {
-      if (lane == k) x *= dinv;
-      float yk = __shfl_sync(kFull, x, k);
-      if (lane > k && lane < NV) x = __fmaf_rn(-h[k], yk, x);
+      if (lane == k) x *= dv[k];
+      const float yk = __shfl_sync(kFull, x, k);
+      if (lane > k && lane < NV) x = __fmaf_rn(-L[lane * G::MS + k], yk, x);
     }
-#pragma unroll
+#pragma unroll 1
     for (int k = NV - 1; k >= 0; --k) {
-      if (lane == k) x *= dinv;
-      float zk = __shfl_sync(kFull, x, k);
+      if (lane == k) x *= dv[k];
+      const float zk = __shfl_sync(kFull, x, k);
       if (lane < k) x = __fmaf_rn(-L[k * G::MS + lane], zk, x);
     }
     return (lane < NV) ? x : 0.f;
@@ -303,12 +315,11 @@ struct WarpSolver {
     const float* Mm = Ms();
     float* L = Ls();
     if (lane < NV) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k)
-        if (k <= lane) L[lane * G::MS + k] = Mm[lane * G::MS + k];
+#pragma unroll 1
+      for (int k = 0; k <= lane; ++k) L[lane * G::MS + k] = Mm[lane * G::MS + k];
     }
     __syncwarp();
-    return factor_from_Ls();
+    return factor();
   }
 
   // H = M + sum_{active} D_i J_i^T J_i (Eq. 9) into Ls(), then factor.
@@ -322,16 +333,39 @@ struct WarpSolver {
     if (lane < G::NBLK) {
       int bj = 0;
       while ((bj + 1) * (bj + 2) / 2 <= lane) ++bj;
-      int bk = lane - bj * (bj + 1) / 2;
+      const int bk = lane - bj * (bj + 1) / 2;
       float acc[G::BS][G::BS];
 #pragma unroll
       for (int u = 0; u < G::BS; ++u)
 #pragma unroll
         for (int v = 0; v < G::BS; ++v) acc[u][v] = 0.f;
       const int cj = bj * G::BS, ck = bk * G::BS;
-      for (int q = 0; q < nact; ++q) {
-        int i = idx[q];
-        float d = Dm[i];
+      // two rows per pass: their loads issue back to back
+      int q = 0;
+#pragma unroll 1
+      for (; q + 2 <= nact; q += 2) {
+        float x[2][G::BS], y[2][G::BS];
+#pragma unroll
+        for (int r2 = 0; r2 < 2; ++r2) {
+          const int i = idx[q + r2];
+          const float d = Dm[i];
+          const float* Ji = Jm + i * G::JS;
+#pragma unroll
+          for (int u = 0; u < G::BS; ++u) x[r2][u] = Ji[cj + u] * d;
+#pragma unroll
+          for (int v = 0; v < G::BS; ++v) y[r2][v] = Ji[ck + v];
+        }
+#pragma unroll
+        for (int r2 = 0; r2 < 2; ++r2)
+#pragma unroll
+          for (int u = 0; u < G::BS; ++u)
+#pragma unroll
+            for (int v = 0; v < G::BS; ++v)
+              acc[u][v] = __fmaf_rn(x[r2][u], y[r2][v], acc[u][v]);
+      }
+      if (q < nact) {
+        const int i = idx[q];
+        const float d = Dm[i];
         const float* Ji = Jm + i * G::JS;
         float x[G::BS], y[G::BS];
 #pragma unroll
@@ -347,12 +381,12 @@ struct WarpSolver {
       for (int u = 0; u < G::BS; ++u)
 #pragma unroll
         for (int v = 0; v < G::BS; ++v) {
-          int rr = cj + u, cc = ck + v;
+          const int rr = cj + u, cc = ck + v;
           if (rr < NV && cc <= rr) L[rr * G::MS + cc] = Mm[rr * G::MS + cc] + acc[u][v];
         }
     }
     __syncwarp();
-    bool ok = factor_from_Ls();
+    const bool ok = factor();
     fmask_bits = act_bits;
     fmask_valid = true;
     return ok;
@@ -363,6 +397,56 @@ struct WarpSolver {
     return __any_sync(kFull, !fmask_valid || (act_bits != fmask_bits));
   }
 
+  // ------------------------------------------------- compensated products
+  // s[t] + c[t] = J_i . (vh + vl) for the rows of this lane.
+  __device__ __forceinline__ void rows_dot2(const float* vh, const float* vl, float (&s)[MT],
+                                            float (&c)[MT]) {
+    const float* Jm = Js() + lane * G::JS;
+#pragma unroll
+    for (int t = 0; t < MT; ++t) { s[t] = 0.f; c[t] = 0.f; }
+#pragma unroll 1
+    for (int k = 0; k < NV; ++k) {
+      const float xh = vh[k], xl = vl[k];
+#pragma unroll
+      for (int t = 0; t < MT; ++t)
+        if (32 * t < m) dot2(s[t], c[t], Jm[32 * t * G::JS + k], xh, xl);
+    }
+  }
+
+  // (s, c) = sum over active rows i of J_ij v_i, for lane j (compensated).
+  __device__ __forceinline__ void jt_active(const float* v, float& s, float& c) {
+    const float* Jm = Js();
+    const int* idx = Idx();
+    float s2 = 0.f, c2 = 0.f;
+    s = 0.f;
+    c = 0.f;
+    if (lane < NV) {
+      int q = 0;
+#pragma unroll 1
+      for (; q + 1 < nact; q += 2) {
+        const int i0 = idx[q], i1 = idx[q + 1];
+        dot2s(s, c, Jm[i0 * G::JS + lane], v[i0]);
+        dot2s(s2, c2, Jm[i1 * G::JS + lane], v[i1]);
+      }
+      if (q < nact) {
+        const int i0 = idx[q];
+        dot2s(s, c, Jm[i0 * G::JS + lane], v[i0]);
+      }
+      add_pair(s, c, s2, c2);
+    }
+  }
+
+  // (s, c) = (M (vh + vl))_j for lane j (compensated).
+  __device__ __forceinline__ void m_times(const float* vh, const float* vl, float& s, float& c) {
+    s = 0.f;
+    c = 0.f;
+    if (lane < NV) {
+      const float* Mr = Ms() + lane * G::MS;
+#pragma unroll 1
+      for (int k = 0; k < NV; ++k) dot2(s, c, Mr[k], vh[k], vl[k]);
+    }
+  }
+
   // --------------------------------------------------------- residual
   // At a = ah + al: jar (compensated), active set, f, active row list,
   // r = M a - qfrc + J^T f (compensated), maq = M a - qfrc.
@@ -370,19 +454,10 @@ struct WarpSolver {
   __device__ __forceinline__ float residual(float* scale, bool* bad) {
     put_vec(V_AH, ah);
     put_vec(V_AL, al);
-    const float* Jm = Js();
     const float* vh = Vec(V_AH);
     const float* vl = Vec(V_AL);
     float s[MT], c[MT];
-#pragma unroll
-    for (int t = 0; t < MT; ++t) { s[t] = 0.f; c[t] = 0.f; }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      float xh = vh[k], xl = vl[k];
-#pragma unroll
-      for (int t = 0; t < MT; ++t)
-        if (32 * t < m) dot2(s[t], c[t], Jm[(lane + 32 * t) * G::JS + k], xh, xl);
-    }
+    rows_dot2(vh, vl, s, c);
     act_bits = 0;
     float* F = Fs();
     int* idx = Idx();
@@ -394,11 +469,11 @@ struct WarpSolver {
         float u, ue;
         two_sum(s[t], -aref_r[t], u, ue);
         jar_r[t] = u + (ue + c[t]);
-        bool on = row_valid(t) && jar_r[t] < 0.f;
-        float f = on ? D_r[t] * jar_r[t] : 0.f;
+        const bool on = row_valid(t) && jar_r[t] < 0.f;
+        const float f = on ? D_r[t] * jar_r[t] : 0.f;
         if (row_valid(t)) F[lane + 32 * t] = f;
         fm = fmaxf(fm, fabsf(f));
-        unsigned bal = __ballot_sync(kFull, on);
+        const unsigned bal = __ballot_sync(kFull, on);
         if (on) {
           act_bits |= 1u << t;
           idx[base + __popc(bal & ((1u << lane) - 1u))] = lane + 32 * t;
@@ -409,26 +484,21 @@ struct WarpSolver {
     nact = base;
     fmax = warp_max(fm);
     __syncwarp();
-    // (M a)_j and (J^T f)_j, compensated, lane j
-    float ms = 0.f, mc = 0.f, js = 0.f, jc = 0.f;
-    if (lane < NV) {
-      const float* Mr = Ms() + lane * G::MS;
-#pragma unroll
-      for (int k = 0; k < NV; ++k) dot2(ms, mc, Mr[k], vh[k], vl[k]);
-      for (int q = 0; q < nact; ++q) {
-        int i = idx[q];
-        dot2s(js, jc, Jm[i * G::JS + lane], F[i]);
-      }
-    }
+    float js, jc, ms, mc;
+    jt_active(F, js, jc);
+    m_times(vh, vl, ms, mc);
     float t1, e1, t2, e2;
     two_sum(ms, -qf, t1, e1);
-    float lo1 = __fadd_rn(e1, mc);
+    const float lo1 = __fadd_rn(e1, mc);
     maq = __fadd_rn(t1, lo1);
     two_sum(t1, js, t2, e2);
     r = __fadd_rn(t2, __fadd_rn(lo1, __fadd_rn(e2, jc)));
-    if (lane >= NV) { r = 0.f; maq = 0.f; }
-    float rm = warp_max(fabsf(r));
-    float sc = fmaxf(fmaxf(1.f, qmax), fmaxf(warp_max(fabsf(ms)), warp_max(fabsf(js))));
+    if (lane >= NV) {
+      r = 0.f;
+      maq = 0.f;
+    }
+    const float rm = warp_max(fabsf(r));
+    const float sc = fmaxf(fmaxf(1.f, qmax), fmaxf(warp_max(fabsf(ms)), warp_max(fabsf(js))));
     *scale = sc;
     *bad = __any_sync(kFull, !(fabsf(r) < CUDART_INF_F)) || !(sc < CUDART_INF_F);
     return rm;
@@ -441,37 +511,35 @@ struct WarpSolver {
   // linear and strictly increasing.  Also leaves s_r = J p.
   __device__ __forceinline__ float line_search(float p, float* dfmax) {
     put_vec(V_P, p);
-    const float* Jm = Js();
+    const float* Jm = Js() + lane * G::JS;
     const float* vp = Vec(V_P);
 #pragma unroll
     for (int t = 0; t < MT; ++t) s_r[t] = 0.f;
-#pragma unroll
+    float Mp = 0.f;
+    const float* Mr = Ms() + min(lane, NV - 1) * G::MS;
+#pragma unroll 1
     for (int k = 0; k < NV; ++k) {
-      float pk = vp[k];
+      const float pk = vp[k];
 #pragma unroll
       for (int t = 0; t < MT; ++t)
-        if (32 * t < m) s_r[t] = __fmaf_rn(Jm[(lane + 32 * t) * G::JS + k], pk, s_r[t]);
+        if (32 * t < m) s_r[t] = __fmaf_rn(Jm[32 * t * G::JS + k], pk, s_r[t]);
+      Mp = __fmaf_rn(Mr[k], pk, Mp);
     }
-    float Mp = 0.f;
-    if (lane < NV) {
-      const float* Mr = Ms() + lane * G::MS;
-#pragma unroll
-      for (int k = 0; k < NV; ++k) Mp = __fmaf_rn(Mr[k], vp[k], Mp);
-    }
-    const float pMp = warp_sum(p * Mp);
+    const float pMp = warp_sum(lane < NV ? p * Mp : 0.f);
     const float c0 = warp_sum(p * maq);
     float bp[MT];
 #pragma unroll
     for (int t = 0; t < MT; ++t)
-      bp[t] = (row_valid(t) && s_r[t] != 0.f) ? -jar_r[t] / s_r[t] : CUDART_INF_F;
+      bp[t] = (row_valid(t) && s_r[t] != 0.f) ? __fdividef(-jar_r[t], s_r[t]) : CUDART_INF_F;
     float alpha = 1.f, lo = 0.f, hi = CUDART_INF_F;
+#pragma unroll 1
     for (int it = 0; it < kLineSearchMax; ++it) {
       float sum = 0.f, cp = 0.f, cm = 0.f;
 #pragma unroll
       for (int t = 0; t < MT; ++t) {
         if (row_valid(t)) {
-          float u = __fmaf_rn(alpha, s_r[t], jar_r[t]);
-          float ds = D_r[t] * s_r[t];
+          const float u = __fmaf_rn(alpha, s_r[t], jar_r[t]);
+          const float ds = D_r[t] * s_r[t];
           if (u < 0.f) sum = __fmaf_rn(ds, u, sum);
           if (u < 0.f || (u == 0.f && s_r[t] < 0.f)) cp = __fmaf_rn(ds, s_r[t], cp);
           if (u < 0.f || (u == 0.f && s_r[t] > 0.f)) cm = __fmaf_rn(ds, s_r[t], cm);
@@ -498,7 +566,10 @@ struct WarpSolver {
 #pragma unroll
       for (int t = 0; t < MT; ++t)
         cnt += __popc(__ballot_sync(kFull, bp[t] > x0 && bp[t] < x1));
-      if (cnt == 0 && an > 0.f) { alpha = an; break; }
+      if (cnt == 0 && an > 0.f) {
+        alpha = an;
+        break;
+      }
       if (!(an > lo && an < hi)) an = (hi == CUDART_INF_F) ? 2.f * alpha : 0.5f * (lo + hi);
       alpha = an;
       if (it == kLineSearchMax - 1) alpha = (lo > 0.f) ? lo : alpha;
@@ -512,13 +583,13 @@ struct WarpSolver {
     return alpha;
   }
 
-  // a += dp, kept as a normalised float pair.
-  __device__ __forceinline__ void add_to_a(float dp) {
+  // v += dv, kept as a normalised float pair (vh, vl).
+  __device__ __forceinline__ static void add_to_pair(float& vh, float& vl, float dv) {
     float s, e;
-    two_sum(ah, dp, s, e);
-    float lo = __fadd_rn(al, e);
-    ah = __fadd_rn(s, lo);
-    al = __fsub_rn(lo, __fsub_rn(ah, s));
+    two_sum(vh, dv, s, e);
+    const float lo = __fadd_rn(vl, e);
+    vh = __fadd_rn(s, lo);
+    vl = __fsub_rn(lo, __fsub_rn(vh, s));
   }
 
   // --------------------------------------------------------- forward solve
@@ -534,30 +605,31 @@ struct WarpSolver {
     al = 0.f;
     uint32_t prev_bits = 0;
     bool prev_small = false;
+#pragma unroll 1
     for (int k = 0;; ++k) {
       float scale;
       bool bad;
-      float rmax = residual(&scale, &bad);
+      const float rmax = residual(&scale, &bad);
       if (bad) return CS_ST_NONFINITE;
       if (rmax <= P.tol * scale) return CS_ST_OK;
-      bool same = !__any_sync(kFull, act_bits != prev_bits);
+      const bool same = !__any_sync(kFull, act_bits != prev_bits);
       if (k > 0 && same && prev_small) return CS_ST_OK;
       if (k >= P.max_iter) return CS_ST_MAXITER;
       if (need_refactor())
         if (!assemble_and_factor()) return CS_ST_CHOLFAIL;
-      float p = -chol_solve(r);
-      float ptr = warp_sum(p * r);
-      float amax = warp_max(fabsf(ah));
+      const float p = -chol_solve(r);
+      const float ptr = warp_sum(p * r);
+      const float amax = warp_max(fabsf(ah));
       if (!(ptr < 0.f)) {
-        float pm = warp_max(fabsf(p));
+        const float pm = warp_max(fabsf(p));
         return (pm <= kStepTol * amax) ? CS_ST_OK : CS_ST_NOPROGRESS;
       }
       float dfm;
-      float alpha = line_search(p, &dfm);
-      float dp = alpha * p;
-      add_to_a(dp);
+      const float alpha = line_search(p, &dfm);
+      const float dp = alpha * p;
+      add_to_pair(ah, al, dp);
       *iters = k + 1;
-      float smax = warp_max(fabsf(dp));
+      const float smax = warp_max(fabsf(dp));
       prev_small = (smax <= kStepTol * amax) && (dfm <= kForceTol * fmax);
       prev_bits = act_bits;
     }
@@ -570,34 +642,25 @@ struct WarpSolver {
   __device__ __forceinline__ void adjoint(float& wh, float& wl) {
     wh = chol_solve(gj);
     wl = 0.f;
-    const float* Jm = Js();
     float* Lm = Lam();
-    const int* idx = Idx();
     float lam_prev[MT];
 #pragma unroll
     for (int t = 0; t < MT; ++t) lam_prev[t] = 0.f;
     float dmax_prev = CUDART_INF_F;
+#pragma unroll 1
     for (int it = 0; it <= kAdjointRefineMax; ++it) {
       put_vec(V_WH, wh);
       put_vec(V_WL, wl);
       const float* vh = Vec(V_WH);
       const float* vl = Vec(V_WL);
       float s[MT], c[MT];
-#pragma unroll
-      for (int t = 0; t < MT; ++t) { s[t] = 0.f; c[t] = 0.f; }
-#pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        float xh = vh[k], xl = vl[k];
-#pragma unroll
-        for (int t = 0; t < MT; ++t)
-          if (32 * t < m) dot2(s[t], c[t], Jm[(lane + 32 * t) * G::JS + k], xh, xl);
-      }
+      rows_dot2(vh, vl, s, c);
       float lmax = 0.f, dl = 0.f;
 #pragma unroll
       for (int t = 0; t < MT; ++t) {
         if (32 * t < m) {
-          bool on = (act_bits >> t) & 1u;
-          float lam = on ? D_r[t] * __fadd_rn(s[t], c[t]) : 0.f;
+          const bool on = (act_bits >> t) & 1u;
+          const float lam = on ? D_r[t] * __fadd_rn(s[t], c[t]) : 0.f;
           if (row_valid(t)) Lm[lane + 32 * t] = lam;
           lmax = fmaxf(lmax, fabsf(lam));
           dl = fmaxf(dl, fabsf(lam - lam_prev[t]));
@@ -608,34 +671,23 @@ struct WarpSolver {
       dl = warp_max(dl);
       __syncwarp();
       if (it > 0) {
-        float wmax = warp_max(fabsf(wh));
+        const float wmax = warp_max(fabsf(wh));
         if ((dmax_prev <= kStepTol * wmax && dl <= kForceTol * lmax) ||
             it == kAdjointRefineMax)
           break;
       }
       // rho = g - M w - J^T lambda (compensated)
-      float ms = 0.f, mc = 0.f, js = 0.f, jc = 0.f;
-      if (lane < NV) {
-        const float* Mr = Ms() + lane * G::MS;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) dot2(ms, mc, Mr[k], vh[k], vl[k]);
-        for (int q = 0; q < nact; ++q) {
-          int i = idx[q];
-          dot2s(js, jc, Jm[i * G::JS + lane], Lm[i]);
-        }
-      }
+      float js, jc, ms, mc;
+      jt_active(Lm, js, jc);
+      m_times(vh, vl, ms, mc);
       float t1, e1, t2, e2;
       two_sum(gj, -ms, t1, e1);
       two_sum(t1, -js, t2, e2);
       float rho = __fadd_rn(t2, __fsub_rn(__fadd_rn(e1, e2), __fadd_rn(mc, jc)));
       if (lane >= NV) rho = 0.f;
-      float dw = chol_solve(rho);
+      const float dw = chol_solve(rho);
       dmax_prev = warp_max(fabsf(dw));
-      float s2, e3;
-      two_sum(wh, dw, s2, e3);
-      float lo = __fadd_rn(wl, e3);
-      wh = __fadd_rn(s2, lo);
-      wl = __fsub_rn(lo, __fsub_rn(wh, s2));
+      add_to_pair(wh, wl, dw);
     }
     __syncwarp();
   }
@@ -654,10 +706,16 @@ struct WarpSolver {
     const float* va = Vec(V_X);
     float* dJ = P.dJ + e.off_J;
     const int mnv = m * nv;
+#pragma unroll 1
     for (int q = lane; q < mnv; q += 32) {
       int rr, cc;
-      if (nv == NV) { rr = q / NV; cc = q - rr * NV; }
-      else { rr = q / nv; cc = q - rr * nv; }
+      if (nv == NV) {
+        rr = q / NV;
+        cc = q - rr * NV;
+      } else {
+        rr = q / nv;
+        cc = q - rr * nv;
+      }
       dJ[q] = -__fmaf_rn(F[rr], vw[cc], Lm[rr] * va[cc]);
     }
   }
@@ -666,29 +724,34 @@ struct WarpSolver {
   // nv x nv block; padded rows are the identity).
   __device__ __forceinline__ void load_factor(const float* Lp) {
     float* L = Ls();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      float v = 0.f;
-      if (lane < NV && k <= lane) {
+    if (lane < NV) {
+#pragma unroll 1
+      for (int k = 0; k <= lane; ++k) {
+        float v;
         if (lane < nv) v = __ldg(Lp + lane * (lane + 1) / 2 + k);
         else v = (k == lane) ? 1.f : 0.f;
+        L[lane * G::MS + k] = v;
       }
-      h[k] = v;
-    }
-    if (lane < NV) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) L[lane * G::MS + k] = h[k];
     }
     __syncwarp();
-    if (lane < NV) dinv = 1.0f / L[lane * G::MS + lane];
+    if (lane < NV) Vec(V_DINV)[lane] = 1.0f / L[lane * G::MS + lane];
+    __syncwarp();
   }
 
   __device__ __forceinline__ void store_factor(float* Lp) {
+    const float* L = Ls();
     if (lane < nv) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k)
-        if (k <= lane) Lp[lane * (lane + 1) / 2 + k] = h[k];
+#pragma unroll 1
+      for (int k = 0; k <= lane; ++k) Lp[lane * (lane + 1) / 2 + k] = L[lane * G::MS + k];
     }
+  }
+
+  __device__ __forceinline__ void zero_grads(const Params& P, const cs_inst& e) {
+    if (lane < nv) P.dqfrc[e.off_v + lane] = 0.f;
+#pragma unroll 1
+    for (int i = lane; i < m; i += 32) P.daref[e.off_r + i] = 0.f;
+#pragma unroll 1
+    for (int q = lane; q < m * nv; q += 32) P.dJ[e.off_J + q] = 0.f;
   }
 
   // ------------------------------------------------------------ drivers
@@ -705,7 +768,7 @@ struct WarpSolver {
     if (MODE == MODE_FWD || MODE == MODE_FUSED) {
       gj = (MODE == MODE_FUSED && lane < nv) ? __ldg(P.g + e.off_v + lane) : 0.f;
       int iters = 0;
-      int st = forward(P, &iters);
+      const int st = forward(P, &iters);
       if (lane < nv) P.a[e.off_v + lane] = ah;
       if (lane == 0) {
         P.status[b] = st;
@@ -742,7 +805,7 @@ struct WarpSolver {
       write_grads(P, e, wh);
     } else {  // MODE_ADJ
       gj = (lane < nv) ? __ldg(P.g + e.off_v + lane) : 0.f;
-      int st0 = P.status[b];
+      const int st0 = P.status[b];
       if (st0 == CS_ST_CHOLFAIL || st0 == CS_ST_NONFINITE || st0 == CS_ST_BADSHAPE) {
         zero_grads(P, e);
         return;
@@ -774,12 +837,6 @@ struct WarpSolver {
       write_grads(P, e, wh);
     }
   }
-
-  __device__ __forceinline__ void zero_grads(const Params& P, const cs_inst& e) {
-    if (lane < nv) P.dqfrc[e.off_v + lane] = 0.f;
-    for (int i = lane; i < m; i += 32) P.daref[e.off_r + i] = 0.f;
-    for (int q = lane; q < m * nv; q += 32) P.dJ[e.off_J + q] = 0.f;
-  }
 };
 
 // One warp per instance; warps claim instances dynamically (counter) or in a
@@ -795,13 +852,14 @@ __global__ void __launch_bounds__(256) warp_solve_kernel(const __grid_constant__
   const int wpb = blockDim.x >> 5;
   int idx = blockIdx.x * wpb + warp;
   const int stride = gridDim.x * wpb;
-  for (int guard = 0; guard <= P.n; ++guard) {
+#pragma unroll 1
+  for (int guard = 0; guard <= P.n_work; ++guard) {
     if (P.counter) {
       int v = 0;
       if (S.lane == 0) v = atomicAdd(P.counter, 1);
       idx = __shfl_sync(kFull, v, 0);
     }
-    if (idx >= P.n) break;
+    if (idx >= P.n_work) break;
     const int b = P.order ? P.order[idx] : idx;
     if (b >= 0 && b < P.n) S.template run<MODE>(P, b);
     __syncwarp();

@@ -224,3 +224,71 @@ def cost_order(inst_host: np.ndarray) -> np.ndarray:
     m = inst_host["m"].astype(np.int64)
     cost = m * nv * nv + nv ** 3
     return np.argsort(-cost, kind="stable").astype(np.int32)
+
+
+class FusedPlan:
+    """cs_plan for the fused path on one batch: per-(nv, m) bucket kernels,
+    cost-ordered claims, autotuned warps per block, one CUDA graph.
+
+    The plan keeps references to the batch, g and the output tensors it was
+    made for; ``launch()`` re-runs the whole fused solve on them.
+    """
+
+    def __init__(self, batch: DeviceBatch, g, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
+                 autotune=True, graph=True, warps_per_block=0, out: FusedOut | None = None):
+        lib = _lib.load()
+        self.batch = batch
+        self.g = g.contiguous()
+        self.out = out if out is not None else alloc_fused(batch)
+        self._b = batch.cstruct()
+        self._o = options(tol, max_iter, True, warps_per_block)
+        self._inst_host = np.ascontiguousarray(batch.inst_host)
+        flags = ((_lib.CS_PLAN_AUTOTUNE if autotune else 0) |
+                 (_lib.CS_PLAN_GRAPH if graph else 0))
+        h = ctypes.c_void_p(None)
+        o = self.out
+        _lib.check(lib.cs_plan_create_fused(
+            ctypes.byref(self._b), ctypes.byref(self._o),
+            self._inst_host.ctypes.data_as(ctypes.c_void_p), _ptr(self.g), _ptr(o.a),
+            _ptr(o.dqfrc), _ptr(o.daref), _ptr(o.dJ), _ptr(o.status), _ptr(o.iters), flags,
+            _stream(), ctypes.byref(h)), "cs_plan_create_fused")
+        self._h = h
+        self._lib = lib
+
+    def launch(self):
+        _lib.check(self._lib.cs_plan_launch(self._h, _stream()), "cs_plan_launch")
+        return self.out
+
+    def describe(self) -> dict:
+        info = _lib.CsPlanInfo()
+        _lib.check(self._lib.cs_plan_describe(self._h, ctypes.byref(info)), "cs_plan_describe")
+        k = info.n_kernels
+        return {"kernels": k, "graph": bool(info.graph),
+                "buckets": [{"nv_bucket": info.nv_bucket[i], "rows_per_lane": info.rows_per_lane[i],
+                             "instances": info.instances[i],
+                             "warps_per_block": info.warps_per_block[i],
+                             "tuned_ms": round(float(info.tuned_ms[i]), 4)} for i in range(k)]}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            torch.cuda.synchronize()
+            self._lib.cs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_cache_dump() -> str:
+    lib = _lib.load()
+    n = lib.cs_autotune_cache_dump(None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    lib.cs_autotune_cache_dump(buf, n + 1)
+    return buf.value.decode()
+
+
+def autotune_cache_load(text: str) -> int:
+    return int(_lib.load().cs_autotune_cache_load(text.encode()))

@@ -51,6 +51,28 @@ def run_gpu_split(batch, w, keep_factor=True, **kw):
                 a_lo=st.a_lo.cpu().numpy())
 
 
+def valid_mask(w):
+    """Boolean masks of the real (non-padding) entries of the packed arrays."""
+    mv = np.zeros(w.qfrc.size, bool)
+    mr = np.zeros(w.aref.size, bool)
+    mJ = np.zeros(w.J.size, bool)
+    for e in w.inst:
+        nv, m = int(e["nv"]), int(e["m"])
+        mv[e["off_v"]:e["off_v"] + nv] = True
+        mr[e["off_r"]:e["off_r"] + m] = True
+        mJ[e["off_J"]:e["off_J"] + m * nv] = True
+    return dict(a=mv, dqfrc=mv, a_lo=mv, daref=mr, act=mr, dJ=mJ)
+
+
+def valid(w, out, key, masks=None):
+    """The real entries of a packed output (or per-instance array as is)."""
+    masks = masks or valid_mask(w)
+    x = np.asarray(out[key])
+    if key in masks:
+        return x[:masks[key].size][masks[key]]
+    return x[:w.n]
+
+
 def compare(w, gpu, ref, idx, check_act=True):
     """Per-instance comparison; returns a summary dict (fails nothing)."""
     worst = dict(a=0.0, dqfrc=0.0, daref=0.0, dJ=0.0)

@@ -1,0 +1,112 @@
+"""The C ABI library loads on a machine without a GPU, exports every entry
+point its header declares, and rejects bad arguments on the host (before any
+CUDA call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2607_24959_b300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if build.is_stale():
+        build.build()
+    return _lib.load()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(cs_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"cs_solve_fwd", "cs_solve_adjoint", "cs_solve_fused"} <= names
+    raw = ctypes.CDLL(_lib.LIB_PATH)
+    missing = [n for n in sorted(names) if not hasattr(raw, n)]
+    assert not missing, missing
+    unbound = [n for n in sorted(names) if n not in _lib._SIGS]
+    assert not unbound, unbound
+
+
+def test_struct_sizes_match_header(lib):
+    assert ctypes.sizeof(_lib.CsBatch) == 96
+    assert ctypes.sizeof(_lib.CsOptions) == 16
+    assert ctypes.sizeof(_lib.CsState) == 40
+    from paper_2607_24959_b300.workloads import INST_DTYPE
+    assert INST_DTYPE.itemsize == 40
+
+
+def _batch(**kw):
+    b = _lib.CsBatch()
+    b.n, b.nv_max, b.m_max = 4, 18, 128
+    fake = 0x10000
+    b.inst = b.M = b.J = b.qfrc = b.aref = b.D = fake
+    b.total_M = b.total_J = b.total_v = b.total_r = 1000
+    for k, v in kw.items():
+        setattr(b, k, v)
+    return b
+
+
+def _opts(**kw):
+    o = _lib.CsOptions()
+    o.tol, o.max_iter, o.keep_factor, o.warps_per_block = 1e-8, 50, 1, 0
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _fused(lib, b, o, ws_bytes=256, ws=0x20000):
+    f = 0x30000
+    return lib.cs_solve_fused(ctypes.byref(b), ctypes.byref(o), f, None, f, f, f, f, f, f,
+                              ws, ws_bytes, None)
+
+
+def test_host_validation_codes(lib):
+    assert _fused(lib, _batch(n=-1), _opts()) == _lib.CS_EINVAL
+    assert _fused(lib, _batch(n=0), _opts()) == _lib.CS_OK        # no-op, no CUDA
+    assert _fused(lib, _batch(nv_max=33), _opts()) == _lib.CS_EUNSUPPORTED
+    assert _fused(lib, _batch(nv_max=0), _opts()) == _lib.CS_EUNSUPPORTED
+    assert _fused(lib, _batch(m_max=257), _opts()) == _lib.CS_EUNSUPPORTED
+    assert _fused(lib, _batch(M=None), _opts()) == _lib.CS_EINVAL
+    assert _fused(lib, _batch(J=None), _opts()) == _lib.CS_EINVAL
+    assert _fused(lib, _batch(total_J=-1), _opts()) == _lib.CS_EINVAL
+    assert _fused(lib, _batch(), _opts(tol=-1.0)) == _lib.CS_EINVAL
+    assert _fused(lib, _batch(), _opts(max_iter=-1)) == _lib.CS_EINVAL
+    assert _fused(lib, _batch(), _opts(warps_per_block=9)) == _lib.CS_EINVAL
+    assert _fused(lib, _batch(), _opts(), ws_bytes=8) == _lib.CS_EINVAL
+    assert _fused(lib, _batch(), _opts(), ws=0x20004) == _lib.CS_EINVAL   # misaligned
+    assert b"workspace" in lib.cs_last_error()
+    assert lib.cs_solve_fwd(None, None, None, None, None) == _lib.CS_EINVAL
+    o = _opts()
+    b = _batch()
+    assert lib.cs_solve_fwd(ctypes.byref(b), ctypes.byref(o), None, None, None) == _lib.CS_EINVAL
+    assert lib.cs_solve_adjoint(ctypes.byref(b), ctypes.byref(o), None, None, None, None,
+                                None, None, None) == _lib.CS_EINVAL
+
+
+def test_strerror_and_version(lib):
+    assert lib.cs_version() >= 100
+    for code in (0, -1, -2, -3, -4, -5, -6, 1):
+        assert lib.cs_strerror(code)
+    assert lib.cs_strerror(-99) == b"unknown error code"
+
+
+def test_python_layer_fails_loudly_without_library(tmp_path):
+    saved = _lib._lib
+    try:
+        _lib._lib = None
+        with pytest.raises(RuntimeError, match="no CPU fallback"):
+            _lib.load(str(tmp_path / "missing.so"))
+    finally:
+        _lib._lib = saved

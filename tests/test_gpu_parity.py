@@ -66,19 +66,146 @@ def test_fused_equals_split_bitwise(cuda_device):
     f = parity.run_gpu_fused(batch, w)
     s1 = parity.run_gpu_split(batch, w, keep_factor=True)
     s0 = parity.run_gpu_split(batch, w, keep_factor=False)
+    masks = parity.valid_mask(w)
     for k in ("a", "dqfrc", "daref", "dJ", "status", "iters"):
-        assert np.array_equal(f[k], s1[k]), k
-        assert np.array_equal(s0[k], s1[k]), k
+        assert np.array_equal(parity.valid(w, f, k, masks), parity.valid(w, s1, k, masks)), k
+        assert np.array_equal(parity.valid(w, s0, k, masks), parity.valid(w, s1, k, masks)), k
 
 
 def test_launch_shape_and_order_do_not_change_results(cuda_device):
     w = W.quadruped(n=900, seed=5)
     batch = solver.DeviceBatch.from_workload(w, cuda_device)
     base = parity.run_gpu_fused(batch, w)
+    masks = parity.valid_mask(w)
     order = torch.from_numpy(solver.cost_order(w.inst)).to(cuda_device)
     rev = torch.flip(torch.arange(w.n, dtype=torch.int32, device=cuda_device), [0])
     for kw in (dict(order=order), dict(order=rev), dict(warps_per_block=1),
                dict(warps_per_block=8)):
         o = parity.run_gpu_fused(batch, w, **kw)
         for k in ("a", "dqfrc", "daref", "dJ", "status", "iters"):
-            assert np.array_equal(o[k], base[k]), (kw, k)
+            assert np.array_equal(parity.valid(w, o, k, masks),
+                                  parity.valid(w, base, k, masks)), (kw, k)
+
+
+def test_plan_matches_single_kernel_bitwise(cuda_device):
+    w = W.quadruped(n=3000, seed=31)
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    g = torch.from_numpy(w.g).to(cuda_device)
+    single = parity.run_gpu_fused(batch, w)
+    plan = solver.FusedPlan(batch, g, autotune=True, graph=True)
+    info = plan.describe()
+    assert info["graph"] and info["kernels"] >= 3, info     # MT 1, 2, 4 buckets
+    assert sum(b["instances"] for b in info["buckets"]) == w.n
+    for _ in range(2):                                       # replays are repeatable
+        out = plan.launch()
+        torch.cuda.synchronize()
+        got = dict(a=out.a.cpu().numpy(), dqfrc=out.dqfrc.cpu().numpy(),
+                   daref=out.daref.cpu().numpy(), dJ=out.dJ.cpu().numpy(),
+                   status=out.status.cpu().numpy(), iters=out.iters.cpu().numpy())
+        masks = parity.valid_mask(w)
+        for k in ("a", "dqfrc", "daref", "dJ", "status", "iters"):
+            assert np.array_equal(parity.valid(w, got, k, masks),
+                                  parity.valid(w, single, k, masks)), k
+    plan.close()
+
+
+def _mixed_workload():
+    parts = []
+    for gen, n in ((lambda: W.tiny(n=200, seed=3), 200),
+                   (lambda: W.franka(n=200, seed=4), 200),
+                   (lambda: W.quadruped(n=200, seed=5), 200),
+                   (lambda: W.generate("nv32", 60, 32, 64, seed=6, cond=1e3), 60),
+                   (lambda: W.generate("nv5", 60, 5, 7, seed=7, cond=1e2), 60),
+                   (lambda: W.generate("nv1", 40, 1, 3, seed=8, cond=1.0), 40)):
+        w = gen()
+        parts += [w.instance(b) for b in range(n)]
+    rng = np.random.default_rng(0)
+    parts = [parts[i] for i in rng.permutation(len(parts))]
+    return W.pack(parts, name="mixed")
+
+
+def test_mixed_nv_plan_parity(cuda_device):
+    w = _mixed_workload()
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    g = torch.from_numpy(w.g).to(cuda_device)
+    plan = solver.FusedPlan(batch, g, autotune=False, graph=True)
+    assert plan.describe()["kernels"] >= 4
+    out = plan.launch()
+    torch.cuda.synchronize()
+    gpu = dict(a=out.a.cpu().numpy(), dqfrc=out.dqfrc.cpu().numpy(),
+               daref=out.daref.cpu().numpy(), dJ=out.dJ.cpu().numpy(),
+               status=out.status.cpu().numpy(), iters=out.iters.cpu().numpy())
+    _check(w, gpu, np.arange(w.n), "mixed nv plan")
+    plan.close()
+
+
+def test_edge_cases(cuda_device):
+    # nc = 0 everywhere (closed form), nv = 1, the largest supported sizes,
+    # offsets that are not multiples of 4 (no 16-byte loads)
+    cases = [W.generate("nc0", 100, 18, 0, seed=9),
+             W.generate("nv1", 50, 1, 2, seed=10, cond=1.0),
+             W.generate("max", 40, 32, 64, seed=11, cond=1e3)]
+    odd = W.generate("odd", 30, 7, 3, seed=12, cond=1e2)
+    parts = [odd.instance(b) for b in range(odd.n)]
+    inst, tM, tJ, tv, tr = W.layout([7] * 30, [12] * 30)
+    # re-pack without alignment padding
+    M = np.concatenate([p["M"].ravel() for p in parts])
+    J = np.concatenate([p["J"].ravel() for p in parts])
+    q = np.concatenate([p["qfrc"] for p in parts])
+    g = np.concatenate([p["g"] for p in parts])
+    ar = np.concatenate([p["aref"] for p in parts])
+    D = np.concatenate([p["D"] for p in parts])
+    inst["off_M"] = np.arange(30) * 49
+    inst["off_J"] = np.arange(30) * 84
+    inst["off_v"] = np.arange(30) * 7
+    inst["off_r"] = np.arange(30) * 12
+    cases.append(W.Workload("unaligned", inst, M, J, q, ar, D, g, {}))
+    for w in cases:
+        batch = solver.DeviceBatch.from_workload(w, cuda_device)
+        _check(w, parity.run_gpu_fused(batch, w), np.arange(w.n), w.name)
+        _check(w, parity.run_gpu_split(batch, w), np.arange(w.n), w.name + " split")
+
+
+def test_max_rows_per_instance(cuda_device):
+    w = W.generate("m256", 64, 18, 64, seed=13, cond=1e3)     # m = 256 rows
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    _check(w, parity.run_gpu_fused(batch, w), np.arange(w.n), "m=256")
+
+
+def test_empty_batch_and_bad_shapes(cuda_device):
+    w = W.quadruped(n=10, seed=14)
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    empty = solver.DeviceBatch(batch.inst, batch.M, batch.J, batch.qfrc, batch.aref,
+                               batch.D, 0, 1, 0, w.inst[:0])
+    g = torch.zeros(4, device=cuda_device)
+    solver.solve_fused(empty, g)                          # no-op, no error
+    # an instance larger than the batch bound is flagged, the others solve
+    inst = w.inst.copy()
+    inst["m"][3] = 200                                    # > m_max of the batch
+    bad = solver.DeviceBatch(torch.from_numpy(inst.view(np.uint8)).to(cuda_device),
+                             batch.M, batch.J, batch.qfrc, batch.aref, batch.D,
+                             w.n, 18, 128, inst)
+    out = solver.solve_fused(bad, torch.from_numpy(w.g).to(cuda_device))
+    torch.cuda.synchronize()
+    st = out.status.cpu().numpy()[:w.n]
+    assert st[3] == 4 and np.all(np.delete(st, 3) == 0), st
+
+
+def test_nonfinite_input_is_a_status(cuda_device):
+    w = W.quadruped(n=20, seed=15)
+    w.qfrc[w.inst["off_v"][5]] = np.nan
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    out = solver.solve_fused(batch, torch.from_numpy(w.g).to(cuda_device))
+    torch.cuda.synchronize()
+    st = out.status.cpu().numpy()[:w.n]
+    assert st[5] == 3 and np.all(np.delete(st, 5) == 0), st
+
+
+def test_iteration_cap_status(cuda_device):
+    w = W.quadruped(n=200, seed=16)
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    out = solver.solve_fused(batch, torch.from_numpy(w.g).to(cuda_device), max_iter=1)
+    torch.cuda.synchronize()
+    st = out.status.cpu().numpy()[:w.n]
+    it = out.iters.cpu().numpy()[:w.n]
+    assert np.all(it <= 1) and np.any(st == 1) and set(np.unique(st)) <= {0, 1}
