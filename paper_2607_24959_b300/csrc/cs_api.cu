@@ -30,7 +30,7 @@ int cuda_error(cudaError_t e, const char* where) {
 
 // Compiled buckets.  nv is padded up to the bucket; m up to 32 * MT.
 static const int kNvBuckets[] = {3, 9, 18, 32};
-static const int kMtBuckets[] = {1, 2, 4, 8};
+static const int kMtBuckets[] = {1, 2, 3, 4, 6, 8};
 
 int nv_bucket(int nv) {
   for (int b : kNvBuckets)

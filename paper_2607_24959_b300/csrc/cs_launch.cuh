@@ -52,7 +52,9 @@ static cudaError_t launch_mt(int mt, const csk::Params& P, const LaunchCfg& cfg,
   switch (mt) {
     case 1: return launch_t<NV, 1, MODE>(P, cfg, s, info);
     case 2: return launch_t<NV, 2, MODE>(P, cfg, s, info);
+    case 3: return launch_t<NV, 3, MODE>(P, cfg, s, info);
     case 4: return launch_t<NV, 4, MODE>(P, cfg, s, info);
+    case 6: return launch_t<NV, 6, MODE>(P, cfg, s, info);
     case 8: return launch_t<NV, 8, MODE>(P, cfg, s, info);
     default: return cudaErrorInvalidValue;
   }

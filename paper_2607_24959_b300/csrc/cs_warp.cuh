@@ -447,17 +447,65 @@ struct WarpSolver {
     }
   }
 
+  // Plain FP32 counterparts, used while the active set is still changing.
+  __device__ __forceinline__ void rows_dot(const float* vh, float (&s)[MT]) {
+    const float* Jm = Js() + lane * G::JS;
+#pragma unroll
+    for (int t = 0; t < MT; ++t) s[t] = 0.f;
+#pragma unroll 1
+    for (int k = 0; k < NV; ++k) {
+      const float xh = vh[k];
+#pragma unroll
+      for (int t = 0; t < MT; ++t)
+        if (32 * t < m) s[t] = __fmaf_rn(Jm[32 * t * G::JS + k], xh, s[t]);
+    }
+  }
+  __device__ __forceinline__ float jt_active_plain(const float* v) {
+    const float* Jm = Js();
+    const int* idx = Idx();
+    float s = 0.f, s2 = 0.f;
+    if (lane < NV) {
+      int q = 0;
+#pragma unroll 1
+      for (; q + 1 < nact; q += 2) {
+        const int i0 = idx[q], i1 = idx[q + 1];
+        s = __fmaf_rn(Jm[i0 * G::JS + lane], v[i0], s);
+        s2 = __fmaf_rn(Jm[i1 * G::JS + lane], v[i1], s2);
+      }
+      if (q < nact) s = __fmaf_rn(Jm[idx[q] * G::JS + lane], v[idx[q]], s);
+    }
+    return s + s2;
+  }
+  __device__ __forceinline__ float m_times_plain(const float* vh) {
+    float s = 0.f;
+    if (lane < NV) {
+      const float* Mr = Ms() + lane * G::MS;
+#pragma unroll 1
+      for (int k = 0; k < NV; ++k) s = __fmaf_rn(Mr[k], vh[k], s);
+    }
+    return s;
+  }
+
   // --------------------------------------------------------- residual
   // At a = ah + al: jar (compensated), active set, f, active row list,
   // r = M a - qfrc + J^T f (compensated), maq = M a - qfrc.
   // Returns max|r|; *scale = max(1, |qfrc|, |Ma|, |J^T f|); *bad = non-finite.
-  __device__ __forceinline__ float residual(float* scale, bool* bad) {
+  //
+  // precise = false evaluates the same quantities in plain FP32 (used while
+  // the active set is still changing, where only the direction matters).
+  __device__ __forceinline__ float residual(float* scale, bool* bad, bool precise = true) {
     put_vec(V_AH, ah);
     put_vec(V_AL, al);
     const float* vh = Vec(V_AH);
     const float* vl = Vec(V_AL);
     float s[MT], c[MT];
-    rows_dot2(vh, vl, s, c);
+    if (precise) {
+      rows_dot2(vh, vl, s, c);
+    } else {
+      rows_dot(vh, s);
+#pragma unroll
+      for (int t = 0; t < MT; ++t) c[t] = 0.f;
+    }
     act_bits = 0;
     float* F = Fs();
     int* idx = Idx();
@@ -485,8 +533,15 @@ struct WarpSolver {
     fmax = warp_max(fm);
     __syncwarp();
     float js, jc, ms, mc;
-    jt_active(F, js, jc);
-    m_times(vh, vl, ms, mc);
+    if (precise) {
+      jt_active(F, js, jc);
+      m_times(vh, vl, ms, mc);
+    } else {
+      js = jt_active_plain(F);
+      ms = m_times_plain(vh);
+      jc = 0.f;
+      mc = 0.f;
+    }
     float t1, e1, t2, e2;
     two_sum(ms, -qf, t1, e1);
     const float lo1 = __fadd_rn(e1, mc);
@@ -509,7 +564,7 @@ struct WarpSolver {
   // lane.  phi'(alpha) = c0 + alpha p^T M p + sum_i D_i s_i min(jar_i + alpha s_i, 0)
   // with c0 = p^T (M a - qfrc) and s = J p; phi' is continuous, piecewise
   // linear and strictly increasing.  Also leaves s_r = J p.
-  __device__ __forceinline__ float line_search(float p, float* dfmax) {
+  __device__ __forceinline__ float line_search(float p, float* dfmax, bool* crossed) {
     put_vec(V_P, p);
     const float* Jm = Js() + lane * G::JS;
     const float* vp = Vec(V_P);
@@ -531,34 +586,35 @@ struct WarpSolver {
 #pragma unroll
     for (int t = 0; t < MT; ++t)
       bp[t] = (row_valid(t) && s_r[t] != 0.f) ? __fdividef(-jar_r[t], s_r[t]) : CUDART_INF_F;
+    // The slope uses the rows strictly active at alpha; a row exactly at its
+    // breakpoint (u == 0) is a measure-zero event whose only effect would be
+    // one more trial.
     float alpha = 1.f, lo = 0.f, hi = CUDART_INF_F;
 #pragma unroll 1
     for (int it = 0; it < kLineSearchMax; ++it) {
-      float sum = 0.f, cp = 0.f, cm = 0.f;
+      float sum = 0.f, cs = 0.f;
 #pragma unroll
       for (int t = 0; t < MT; ++t) {
         if (row_valid(t)) {
           const float u = __fmaf_rn(alpha, s_r[t], jar_r[t]);
           const float ds = D_r[t] * s_r[t];
-          if (u < 0.f) sum = __fmaf_rn(ds, u, sum);
-          if (u < 0.f || (u == 0.f && s_r[t] < 0.f)) cp = __fmaf_rn(ds, s_r[t], cp);
-          if (u < 0.f || (u == 0.f && s_r[t] > 0.f)) cm = __fmaf_rn(ds, s_r[t], cm);
+          if (u < 0.f) {
+            sum = __fmaf_rn(ds, u, sum);
+            cs = __fmaf_rn(ds, s_r[t], cs);
+          }
         }
       }
       sum = warp_sum(sum);
-      cp = warp_sum(cp);
-      cm = warp_sum(cm);
+      cs = warp_sum(cs);
       const float d = c0 + alpha * pMp + sum;
       if (d == 0.f) break;
-      float an, x0, x1;
+      float an = alpha - d / (pMp + cs), x0, x1;
       if (d < 0.f) {
         lo = alpha;
-        an = alpha - d / (pMp + cp);
         x0 = alpha;
         x1 = an;
       } else {
         hi = alpha;
-        an = alpha - d / (pMp + cm);
         x0 = an;
         x1 = alpha;
       }
@@ -574,12 +630,17 @@ struct WarpSolver {
       alpha = an;
       if (it == kLineSearchMax - 1) alpha = (lo > 0.f) ? lo : alpha;
     }
-    // largest change of an active force over the step
+    // largest change of an active force over the step, and whether any row
+    // changes side of its breakpoint within (0, alpha)
     float df = 0.f;
+    int cr = 0;
 #pragma unroll
-    for (int t = 0; t < MT; ++t)
+    for (int t = 0; t < MT; ++t) {
       if ((act_bits >> t) & 1u) df = fmaxf(df, fabsf(D_r[t] * alpha * s_r[t]));
+      cr |= (bp[t] > 0.f && bp[t] < alpha) ? 1 : 0;
+    }
     *dfmax = warp_max(df);
+    *crossed = __any_sync(kFull, cr);
     return alpha;
   }
 
@@ -605,12 +666,21 @@ struct WarpSolver {
     al = 0.f;
     uint32_t prev_bits = 0;
     bool prev_small = false;
+    // Plain FP32 residuals while the active set changes; compensated ones
+    // from the first step that crosses no breakpoint on (every stop test and
+    // every returned quantity is taken in the compensated phase).
+    bool precise = false;
 #pragma unroll 1
     for (int k = 0;; ++k) {
       float scale;
       bool bad;
-      const float rmax = residual(&scale, &bad);
+      const float rmax = residual(&scale, &bad, precise);
       if (bad) return CS_ST_NONFINITE;
+      if (!precise && (k >= P.max_iter || rmax <= P.tol * scale)) {
+        precise = true;  // re-evaluate this point accurately before stopping
+        --k;
+        continue;
+      }
       if (rmax <= P.tol * scale) return CS_ST_OK;
       const bool same = !__any_sync(kFull, act_bits != prev_bits);
       if (k > 0 && same && prev_small) return CS_ST_OK;
@@ -625,13 +695,15 @@ struct WarpSolver {
         return (pm <= kStepTol * amax) ? CS_ST_OK : CS_ST_NOPROGRESS;
       }
       float dfm;
-      const float alpha = line_search(p, &dfm);
+      bool crossed;
+      const float alpha = line_search(p, &dfm, &crossed);
       const float dp = alpha * p;
       add_to_pair(ah, al, dp);
       *iters = k + 1;
       const float smax = warp_max(fabsf(dp));
-      prev_small = (smax <= kStepTol * amax) && (dfm <= kForceTol * fmax);
+      prev_small = precise && (smax <= kStepTol * amax) && (dfm <= kForceTol * fmax);
       prev_bits = act_bits;
+      precise = precise || !crossed;
     }
   }
 
