@@ -158,6 +158,36 @@ int cs_solve_fused(const cs_batch* batch, const cs_options* opt,
                    int32_t* iters, void* workspace, size_t workspace_bytes,
                    void* stream);
 
+/* ---- fused solve without any allocation ------------------------------- */
+
+/* Instances cs_solve_fused_static can take in one call. */
+#define CS_STATIC_MAX_INSTANCES (1 << 20)
+
+/* cs_solve_fused for callers that cannot allocate device memory: processes
+ * that may not call cudaMalloc (a host framework owns a fixed pool, or
+ * allocation is forbidden where the call is made) and so cannot provide the
+ * scratch workspace cs_solve_fused takes.  The paper has no counterpart; this
+ * is a deployment variant of the same fused kernel.
+ *
+ * Scratch (the claim counter and the claim order) lives in a static device
+ * array inside the library: about 4 MiB, held on every GPU that loads the
+ * library until the process exits.  The call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  The caller still passes every
+ * input and output, as for cs_solve_fused.  inst_host (a host copy of the
+ * instance table, or NULL) orders the claims by decreasing cost; with NULL
+ * the instances are claimed in index order.
+ *
+ * Limits and sharing: n above CS_STATIC_MAX_INSTANCES returns
+ * CS_EUNSUPPORTED.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  Every call shares the one array and resets the counter
+ * itself; calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race on it and must be serialised by the caller. */
+int cs_solve_fused_static(const cs_batch* batch, const cs_options* opt,
+                          const float* g, const cs_inst* inst_host, float* a,
+                          float* dqfrc, float* daref, float* dJ,
+                          int32_t* status, int32_t* iters, void* stream);
+
 /* ---- execution plans (fused path) ------------------------------------- */
 
 /* Plan flags. */

@@ -85,7 +85,12 @@ _SIGS = {
     "cs_plan_destroy": (None, [c_void_p]),
     "cs_autotune_cache_dump": (ctypes.c_int, [ctypes.c_char_p, c_size_t]),
     "cs_autotune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "cs_solve_fused_static": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
+                                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                             c_void_p, c_void_p, c_void_p, c_void_p]),
 }
+
+STATIC_MAX_INSTANCES = 1 << 20
 
 _lock = threading.Lock()
 _lib = None

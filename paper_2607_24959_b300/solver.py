@@ -215,6 +215,27 @@ def solve_fused(batch: DeviceBatch, g, order=None, tol=DEFAULT_TOL,
     return out
 
 
+def solve_fused_static(batch: DeviceBatch, g, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
+                       warps_per_block=0, cost_ordered=True, out: FusedOut | None = None):
+    """solve_fused without any device allocation by the library: the claim
+    counter and order live in the library's static device array
+    (cs_solve_fused_static).  ``out`` may be preallocated by the caller (its
+    workspace field is not used)."""
+    lib = _lib.load()
+    if out is None:
+        out = alloc_fused(batch)
+    b = batch.cstruct()
+    o = options(tol, max_iter, True, warps_per_block)
+    g = g.contiguous()
+    inst = np.ascontiguousarray(batch.inst_host) if cost_ordered else None
+    _lib.check(lib.cs_solve_fused_static(
+        ctypes.byref(b), ctypes.byref(o), _ptr(g),
+        None if inst is None else inst.ctypes.data_as(ctypes.c_void_p), _ptr(out.a),
+        _ptr(out.dqfrc), _ptr(out.daref), _ptr(out.dJ), _ptr(out.status), _ptr(out.iters),
+        _stream()), "cs_solve_fused_static")
+    return out
+
+
 def cost_order(inst_host: np.ndarray) -> np.ndarray:
     """Claim order for the persistent kernel: most expensive instances first.
 
