@@ -52,7 +52,7 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0, period_ms=200):
+    def __init__(self, index=0, period_ms=50):
         self.index = index
         self.period_ms = period_ms
         self.proc = None
@@ -135,6 +135,10 @@ def make_workload(name, rank, n=None):
         return W.franka(seed=W.SEEDS["franka"] + seed_shift, **kw)
     if name == "tiny":
         return W.tiny(seed=W.SEEDS["tiny"] + seed_shift, **kw)
+    if name == "nv96":
+        return W.nv96(seed=W.SEEDS["nv96"] + seed_shift, **kw)
+    if name == "nc256":
+        return W.nc256(seed=W.SEEDS["nc256"] + 1 + seed_shift, **kw)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -358,8 +362,8 @@ def run_e2e(args, w, batch, dev, kw, world):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="quadruped")
     ap.add_argument("--n", type=int, default=None,

@@ -35,8 +35,12 @@
  *    across the ABI.  cs_last_error() describes the last failure of the
  *    calling thread.  Per-instance numerical outcomes (CS_ST_*) are written to
  *    the status array, never returned.
- *  - Supported sizes: 1 <= nv <= 32 and 0 <= m <= 256 per instance (one warp
- *    per instance).  An instance outside them gets CS_ST_BADSHAPE.
+ *  - Supported sizes: 1 <= nv <= 128 and 0 <= m <= 1024 per instance.  Up to
+ *    nv = 32 and m = 256 one warp solves an instance; beyond, one 256-thread
+ *    CTA does, and nv_max x m_max must then fit one CTA's shared memory
+ *    (about nv_max * (2 nv_max + m_max) * 4 bytes; checked, CS_EUNSUPPORTED
+ *    otherwise).  An instance outside the batch's bounds gets
+ *    CS_ST_BADSHAPE.
  */
 #ifndef CONTACT_SOLVE_H
 #define CONTACT_SOLVE_H
@@ -84,8 +88,8 @@ typedef struct cs_inst {
  * kernel); an instance above them is marked CS_ST_BADSHAPE. */
 typedef struct cs_batch {
   int32_t n;             /* number of instances (0 is a no-op) */
-  int32_t nv_max;        /* max nv over the batch, 1..32 */
-  int32_t m_max;         /* max m over the batch, 0..256 */
+  int32_t nv_max;        /* max nv over the batch, 1..128 */
+  int32_t m_max;         /* max m over the batch, 0..1024 */
   int32_t reserved;
   const cs_inst* inst;   /* device, n entries */
   const float* M;        /* device */
@@ -205,6 +209,8 @@ typedef struct cs_plan_info {
   int32_t instances[8];
   int32_t warps_per_block[8];
   float tuned_ms[8];          /* autotuned time of the bucket alone (0 if not) */
+  int32_t cta[8];             /* 1: one CTA per instance (nv_bucket = its max nv,
+                                 rows_per_lane = rows per thread) */
 } cs_plan_info;
 
 /* Make a plan for the fused forward + adjoint (the work of cs_solve_fused)

@@ -55,7 +55,7 @@ class CsPlanInfo(ctypes.Structure):
     _fields_ = [("n_kernels", c_int32), ("graph", c_int32),
                 ("nv_bucket", c_int32 * 8), ("rows_per_lane", c_int32 * 8),
                 ("instances", c_int32 * 8), ("warps_per_block", c_int32 * 8),
-                ("tuned_ms", c_float * 8)]
+                ("tuned_ms", c_float * 8), ("cta", c_int32 * 8)]
 
 
 CS_PLAN_AUTOTUNE = 1

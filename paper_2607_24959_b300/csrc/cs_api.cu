@@ -83,14 +83,42 @@ cudaError_t launch_warp(int mode, int nv_max, int m_max, const csk::Params& P,
   }
 }
 
+bool uses_warp_kernel(int nv_max, int m_max) { return nv_max <= 32 && m_max <= 256; }
+
+cudaError_t launch_dispatch(int mode, int nv_max, int m_max, const csk::Params& P,
+                            const LaunchCfg& cfg, cudaStream_t s, KernelInfo* info) {
+  if (uses_warp_kernel(nv_max, m_max)) return launch_warp(mode, nv_max, m_max, P, cfg, s, info);
+  return launch_cta(mode, nv_max, m_max, P, s, info);
+}
+
+int launch_error(cudaError_t e, const char* where) {
+  if (e == cudaErrorInvalidConfiguration)
+    return set_error(CS_EUNSUPPORTED, "%s: the instance sizes do not fit one CTA's shared memory",
+                     where);
+  return cuda_error(e, where);
+}
+
 int check_batch(const cs_batch* b, const cs_options* o) {
+  int rc = check_batch_shapes(b, o);
+  if (rc != CS_OK || b->n == 0) return rc;
+  if (!uses_warp_kernel(b->nv_max, b->m_max) &&
+      cta_smem_bytes(b->nv_max, b->m_max) > device_smem_optin())
+    return set_error(CS_EUNSUPPORTED,
+                     "nv_max = %d with m_max = %d needs %zu bytes of shared memory per CTA "
+                     "(limit %zu)",
+                     b->nv_max, b->m_max, cta_smem_bytes(b->nv_max, b->m_max),
+                     device_smem_optin());
+  return CS_OK;
+}
+
+int check_batch_shapes(const cs_batch* b, const cs_options* o) {
   if (!b || !o) return set_error(CS_EINVAL, "batch and options must not be NULL");
   if (b->n < 0) return set_error(CS_EINVAL, "n = %d < 0", b->n);
   if (b->n == 0) return CS_OK;
-  if (b->nv_max < 1 || b->nv_max > 32)
-    return set_error(CS_EUNSUPPORTED, "nv_max = %d outside 1..32", b->nv_max);
-  if (b->m_max < 0 || b->m_max > 256)
-    return set_error(CS_EUNSUPPORTED, "m_max = %d outside 0..256", b->m_max);
+  if (b->nv_max < 1 || b->nv_max > 128)
+    return set_error(CS_EUNSUPPORTED, "nv_max = %d outside 1..128", b->nv_max);
+  if (b->m_max < 0 || b->m_max > 1024)
+    return set_error(CS_EUNSUPPORTED, "m_max = %d outside 0..1024", b->m_max);
   if (!b->inst || !b->M || !b->qfrc)
     return set_error(CS_EINVAL, "inst, M and qfrc must not be NULL");
   if (b->m_max > 0 && (!b->J || !b->aref || !b->D))
@@ -165,9 +193,9 @@ int cs_solve_fwd(const cs_batch* batch, const cs_options* opt, float* a, const c
   P.iters = st->iters;
   LaunchCfg cfg;
   cfg.warps_per_block = opt->warps_per_block;
-  cudaError_t e = launch_warp(csk::MODE_FWD, batch->nv_max, batch->m_max, P, cfg,
-                              (cudaStream_t)stream, nullptr);
-  return e == cudaSuccess ? CS_OK : cuda_error(e, "cs_solve_fwd launch");
+  cudaError_t e = launch_dispatch(csk::MODE_FWD, batch->nv_max, batch->m_max, P, cfg,
+                                  (cudaStream_t)stream, nullptr);
+  return e == cudaSuccess ? CS_OK : launch_error(e, "cs_solve_fwd launch");
 }
 
 int cs_solve_adjoint(const cs_batch* batch, const cs_options* opt, const float* a,
@@ -191,9 +219,9 @@ int cs_solve_adjoint(const cs_batch* batch, const cs_options* opt, const float* 
   P.dJ = dJ;
   LaunchCfg cfg;
   cfg.warps_per_block = opt->warps_per_block;
-  cudaError_t e = launch_warp(csk::MODE_ADJ, batch->nv_max, batch->m_max, P, cfg,
-                              (cudaStream_t)stream, nullptr);
-  return e == cudaSuccess ? CS_OK : cuda_error(e, "cs_solve_adjoint launch");
+  cudaError_t e = launch_dispatch(csk::MODE_ADJ, batch->nv_max, batch->m_max, P, cfg,
+                                  (cudaStream_t)stream, nullptr);
+  return e == cudaSuccess ? CS_OK : launch_error(e, "cs_solve_adjoint launch");
 }
 
 size_t cs_fused_workspace_bytes(int32_t n) {
@@ -228,8 +256,8 @@ int cs_solve_fused(const cs_batch* batch, const cs_options* opt, const float* g,
   if (e != cudaSuccess) return cuda_error(e, "cs_solve_fused counter reset");
   LaunchCfg cfg;
   cfg.warps_per_block = opt->warps_per_block;
-  e = launch_warp(csk::MODE_FUSED, batch->nv_max, batch->m_max, P, cfg, s, nullptr);
-  return e == cudaSuccess ? CS_OK : cuda_error(e, "cs_solve_fused launch");
+  e = launch_dispatch(csk::MODE_FUSED, batch->nv_max, batch->m_max, P, cfg, s, nullptr);
+  return e == cudaSuccess ? CS_OK : launch_error(e, "cs_solve_fused launch");
 }
 
 }  // extern "C"

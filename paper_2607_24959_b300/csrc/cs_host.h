@@ -43,7 +43,20 @@ extern template cudaError_t launch_nv<18>(int, int, const csk::Params&, const La
                                           cudaStream_t, KernelInfo*);
 extern template cudaError_t launch_nv<32>(int, int, const csk::Params&, const LaunchCfg&,
                                           cudaStream_t, KernelInfo*);
+// One CTA per instance (nv > 32 or m > 256; nv <= 128, m <= 1024).
+int cta_rows_per_thread(int m_max);
+size_t cta_smem_bytes(int nv_max, int m_max);
+cudaError_t launch_cta(int mode, int nv_max, int m_max, const csk::Params& P, cudaStream_t s,
+                       KernelInfo* info);
+// Warp kernels when nv_max <= 32 and m_max <= 256, else the CTA kernels.
+bool uses_warp_kernel(int nv_max, int m_max);
+cudaError_t launch_dispatch(int mode, int nv_max, int m_max, const csk::Params& P,
+                            const LaunchCfg& cfg, cudaStream_t s, KernelInfo* info);
+int launch_error(cudaError_t e, const char* where);
+// Argument, shape and option checks; check_batch also checks that a batch
+// solved by one CTA kernel fits its shared memory (plans check per bucket).
 int check_batch(const cs_batch* b, const cs_options* o);
+int check_batch_shapes(const cs_batch* b, const cs_options* o);
 csk::Params make_params(const cs_batch* b, const cs_options* o);
 cudaError_t launch_warp(int mode, int nv_max, int m_max, const csk::Params& P,
                         const LaunchCfg& cfg, cudaStream_t s, KernelInfo* info);

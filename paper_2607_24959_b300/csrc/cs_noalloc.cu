@@ -105,6 +105,6 @@ extern "C" int cs_solve_fused_static(const cs_batch* batch, const cs_options* op
   P.order = inst_host ? order : nullptr;
   LaunchCfg cfg;
   cfg.warps_per_block = opt->warps_per_block;
-  e = launch_warp(csk::MODE_FUSED, batch->nv_max, batch->m_max, P, cfg, s, nullptr);
-  return e == cudaSuccess ? CS_OK : cuda_error(e, "cs_solve_fused_static launch");
+  e = launch_dispatch(csk::MODE_FUSED, batch->nv_max, batch->m_max, P, cfg, s, nullptr);
+  return e == cudaSuccess ? CS_OK : launch_error(e, "cs_solve_fused_static launch");
 }

@@ -26,7 +26,7 @@
 
 #include "contact_solve.h"
 #include "cs_host.h"
-#include "cs_warp.cuh"
+#include "cs_cta.cuh"
 
 namespace cs {
 
@@ -34,6 +34,8 @@ namespace {
 
 struct Bucket {
   int nvb = 0, mt = 0, n = 0, wpb = 2;
+  bool cta = false;      // one CTA per instance (nv > 32 or m > 256)
+  int nv_max = 0, m_max = 0;
   double cost = 0.0;
   float tuned_ms = 0.f;
   int32_t* d_order = nullptr;
@@ -80,8 +82,8 @@ cudaError_t launch_bucket(const cs_plan* p, const Bucket& b, int wpb, cudaStream
   if (e != cudaSuccess) return e;
   LaunchCfg cfg;
   cfg.warps_per_block = wpb;
-  const int nvmax = b.nvb, mmax = 32 * b.mt;
-  return launch_warp(csk::MODE_FUSED, nvmax, mmax, P, cfg, s, nullptr);
+  if (b.cta) return launch_cta(csk::MODE_FUSED, b.nv_max, b.m_max, P, s, nullptr);
+  return launch_warp(csk::MODE_FUSED, b.nvb, 32 * b.mt, P, cfg, s, nullptr);
 }
 
 void destroy_plan(cs_plan* p) {
@@ -149,6 +151,7 @@ int capture_graph(cs_plan* p) {
   }
   for (int i = 0; i < nb && first == cudaSuccess; ++i)
     first = launch_bucket(p, p->buckets[i], p->buckets[i].wpb, p->side[i]);
+  if (first == cudaErrorInvalidConfiguration) first = cudaErrorInvalidValue;
   for (int i = 1; i < nb && first == cudaSuccess; ++i) {
     first = cudaEventRecord(p->ev_join[i], p->side[i]);
     if (first == cudaSuccess) first = cudaStreamWaitEvent(s0, p->ev_join[i], 0);
@@ -179,7 +182,7 @@ int cs_plan_create_fused(const cs_batch* batch, const cs_options* opt, const cs_
                          cs_plan** out) {
   if (!out) return set_error(CS_EINVAL, "out must not be NULL");
   *out = nullptr;
-  int rc = check_batch(batch, opt);
+  int rc = check_batch_shapes(batch, opt);
   if (rc != CS_OK) return rc;
   if (batch->n > 0 && (!inst_host || !g || !a || !dqfrc || !status || !iters ||
                        (batch->m_max > 0 && (!daref || !dJ))))
@@ -199,16 +202,29 @@ int cs_plan_create_fused(const cs_batch* batch, const cs_options* opt, const cs_
 
   // bucket the instances (shapes outside the kernels go to the smallest
   // bucket, where the kernel marks them CS_ST_BADSHAPE)
+  // key (nv bucket, MT) for warp buckets; (-1, rows per thread) for the CTA
+  // buckets, whose shared memory is sized from the bucket's own maxima
   std::map<std::pair<int, int>, std::vector<std::pair<double, int32_t>>> groups;
+  std::map<std::pair<int, int>, std::pair<int, int>> maxima;
   for (int32_t i = 0; i < batch->n; ++i) {
     const cs_inst& e = inst_host[i];
-    int nvb = nv_bucket(e.nv), mt = mt_bucket(e.m);
-    if (e.nv < 1 || e.m < 0 || nvb < 0 || mt < 0 || e.nv > batch->nv_max || e.m > batch->m_max) {
-      nvb = 3;
-      mt = 1;
+    std::pair<int, int> key;
+    const bool bad = e.nv < 1 || e.m < 0 || e.nv > batch->nv_max || e.m > batch->m_max;
+    if (bad) {
+      key = {3, 1};
+    } else if (uses_warp_kernel(e.nv, e.m)) {
+      key = {nv_bucket(e.nv), mt_bucket(e.m)};
+    } else {
+      // CTA buckets by nv (multiples of 32) and rows per thread
+      key = {-((e.nv + 31) / 32), cta_rows_per_thread(e.m)};
     }
     const double nv = e.nv > 0 ? e.nv : 1, m = e.m > 0 ? e.m : 0;
-    groups[{nvb, mt}].push_back({m * nv * nv + nv * nv * nv, i});
+    groups[key].push_back({m * nv * nv + nv * nv * nv, i});
+    auto& mx = maxima[key];
+    if (!bad) {
+      mx.first = std::max(mx.first, e.nv);
+      mx.second = std::max(mx.second, e.m);
+    }
   }
   size_t total = 0;
   for (auto& kv : groups) {
@@ -216,6 +232,10 @@ int cs_plan_create_fused(const cs_batch* batch, const cs_options* opt, const cs_
     b.nvb = kv.first.first;
     b.mt = kv.first.second;
     b.n = (int)kv.second.size();
+    b.cta = b.nvb < 0;
+    b.nv_max = std::max(1, maxima[kv.first].first);
+    b.m_max = maxima[kv.first].second;
+    if (b.cta) b.wpb = csk::kCtaWarps;
     std::stable_sort(kv.second.begin(), kv.second.end(),
                      [](const std::pair<double, int32_t>& x, const std::pair<double, int32_t>& y) {
                        return x.first > y.first;
@@ -227,6 +247,16 @@ int cs_plan_create_fused(const cs_batch* batch, const cs_options* opt, const cs_
   }
   std::sort(p->buckets.begin(), p->buckets.end(),
             [](const Bucket& x, const Bucket& y) { return x.cost > y.cost; });
+  for (const auto& b : p->buckets) {
+    if (b.cta && cta_smem_bytes(b.nv_max, b.m_max) > device_smem_optin()) {
+      const size_t need = cta_smem_bytes(b.nv_max, b.m_max);
+      destroy_plan(p);
+      return set_error(CS_EUNSUPPORTED,
+                       "instances with nv up to %d and m up to %d need %zu bytes of shared "
+                       "memory per CTA (limit %zu)",
+                       b.nv_max, b.m_max, need, device_smem_optin());
+    }
+  }
   if ((int)p->buckets.size() > 8) {
     destroy_plan(p);
     return set_error(CS_EUNSUPPORTED, "more than 8 kernel buckets");
@@ -258,6 +288,7 @@ int cs_plan_create_fused(const cs_batch* batch, const cs_options* opt, const cs_
   }
   // launch geometry: explicit, tuned, cached or default
   for (auto& b : p->buckets) {
+    if (b.cta) continue;
     if (opt->warps_per_block > 0) {
       b.wpb = opt->warps_per_block;
       continue;
@@ -328,6 +359,8 @@ int cs_plan_describe(const cs_plan* p, cs_plan_info* info) {
     info->instances[i] = b.n;
     info->warps_per_block[i] = b.wpb;
     info->tuned_ms[i] = b.tuned_ms;
+    info->cta[i] = b.cta ? 1 : 0;
+    if (b.cta) info->nv_bucket[i] = b.nv_max;
   }
   return CS_OK;
 }

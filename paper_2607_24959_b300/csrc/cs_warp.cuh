@@ -106,7 +106,9 @@ struct Geo {
   static constexpr int oD = oJ + MCAP * JS;          // D   MCAP
   static constexpr int oF = oD + MCAP;               // f   MCAP
   static constexpr int oLam = oF + MCAP;             // lambda = D_act J w
-  static constexpr int oIdx = oLam + MCAP;           // active rows (int)
+  static constexpr int oFlo = oLam + MCAP;           // low parts of f ...
+  static constexpr int oLamlo = oFlo + MCAP;         // ... and of lambda
+  static constexpr int oIdx = oLamlo + MCAP;         // active rows (int)
   static constexpr int oVec = oIdx + MCAP;           // broadcast vectors
   static constexpr int kVec = 7;
   static constexpr int kWords = oVec + kVec * 32;
@@ -164,6 +166,8 @@ struct WarpSolver {
   __device__ __forceinline__ float* Ds() { return sm + G::oD; }
   __device__ __forceinline__ float* Fs() { return sm + G::oF; }
   __device__ __forceinline__ float* Lam() { return sm + G::oLam; }
+  __device__ __forceinline__ float* Flo() { return sm + G::oFlo; }
+  __device__ __forceinline__ float* Lamlo() { return sm + G::oLamlo; }
   __device__ __forceinline__ int* Idx() { return reinterpret_cast<int*>(sm + G::oIdx); }
   __device__ __forceinline__ float* Vec(int s) { return sm + G::oVec + 32 * s; }
 
@@ -413,8 +417,11 @@ struct WarpSolver {
     }
   }
 
-  // (s, c) = sum over active rows i of J_ij v_i, for lane j (compensated).
-  __device__ __forceinline__ void jt_active(const float* v, float& s, float& c) {
+  // (s, c) = sum over active rows i of J_ij (v_i + vlo_i), for lane j
+  // (compensated; v carried as a float pair so that a force computed from a
+  // rounded jar does not put a floor under the residual).
+  __device__ __forceinline__ void jt_active(const float* v, const float* vlo, float& s,
+                                            float& c) {
     const float* Jm = Js();
     const int* idx = Idx();
     float s2 = 0.f, c2 = 0.f;
@@ -425,15 +432,22 @@ struct WarpSolver {
 #pragma unroll 1
       for (; q + 1 < nact; q += 2) {
         const int i0 = idx[q], i1 = idx[q + 1];
-        dot2s(s, c, Jm[i0 * G::JS + lane], v[i0]);
-        dot2s(s2, c2, Jm[i1 * G::JS + lane], v[i1]);
+        dot2(s, c, Jm[i0 * G::JS + lane], v[i0], vlo[i0]);
+        dot2(s2, c2, Jm[i1 * G::JS + lane], v[i1], vlo[i1]);
       }
       if (q < nact) {
         const int i0 = idx[q];
-        dot2s(s, c, Jm[i0 * G::JS + lane], v[i0]);
+        dot2(s, c, Jm[i0 * G::JS + lane], v[i0], vlo[i0]);
       }
       add_pair(s, c, s2, c2);
     }
+  }
+
+  // hi + lo = D * (xh + xl), as a float pair.
+  __device__ __forceinline__ static void scale_pair(float d, float xh, float xl, float& hi,
+                                                    float& lo) {
+    hi = __fmul_rn(d, xh);
+    lo = __fmaf_rn(d, xl, __fmaf_rn(d, xh, -hi));
   }
 
   // (s, c) = (M (vh + vl))_j for lane j (compensated).
@@ -508,6 +522,7 @@ struct WarpSolver {
     }
     act_bits = 0;
     float* F = Fs();
+    float* Fl = Flo();
     int* idx = Idx();
     int base = 0;
     float fm = 0.f;
@@ -516,10 +531,16 @@ struct WarpSolver {
       if (32 * t < m) {
         float u, ue;
         two_sum(s[t], -aref_r[t], u, ue);
-        jar_r[t] = u + (ue + c[t]);
+        const float tl = __fadd_rn(ue, c[t]);
+        jar_r[t] = __fadd_rn(u, tl);
+        const float jlo = __fsub_rn(tl, __fsub_rn(jar_r[t], u));
         const bool on = row_valid(t) && jar_r[t] < 0.f;
-        const float f = on ? D_r[t] * jar_r[t] : 0.f;
-        if (row_valid(t)) F[lane + 32 * t] = f;
+        float f = 0.f, flo = 0.f;
+        if (on) scale_pair(D_r[t], jar_r[t], jlo, f, flo);
+        if (row_valid(t)) {
+          F[lane + 32 * t] = f;
+          Fl[lane + 32 * t] = flo;
+        }
         fm = fmaxf(fm, fabsf(f));
         const unsigned bal = __ballot_sync(kFull, on);
         if (on) {
@@ -534,7 +555,7 @@ struct WarpSolver {
     __syncwarp();
     float js, jc, ms, mc;
     if (precise) {
-      jt_active(F, js, jc);
+      jt_active(F, Fl, js, jc);
       m_times(vh, vl, ms, mc);
     } else {
       js = jt_active_plain(F);
@@ -670,6 +691,12 @@ struct WarpSolver {
     // from the first step that crosses no breakpoint on (every stop test and
     // every returned quantity is taken in the compensated phase).
     bool precise = false;
+    // Once the active set has settled the problem is a fixed quadratic and
+    // the FP32 factor only preconditions it: consecutive such steps are
+    // conjugated (preconditioned CG, Fletcher-Reeves beta), restarted
+    // whenever the active set or the factor changes.
+    bool cg = false;
+    float p_prev = 0.f, zr_prev = 1.f;
 #pragma unroll 1
     for (int k = 0;; ++k) {
       float scale;
@@ -685,10 +712,20 @@ struct WarpSolver {
       const bool same = !__any_sync(kFull, act_bits != prev_bits);
       if (k > 0 && same && prev_small) return CS_ST_OK;
       if (k >= P.max_iter) return CS_ST_MAXITER;
-      if (need_refactor())
+      cg = cg && same;
+      if (need_refactor()) {
         if (!assemble_and_factor()) return CS_ST_CHOLFAIL;
-      const float p = -chol_solve(r);
-      const float ptr = warp_sum(p * r);
+        cg = false;
+      }
+      const float z = chol_solve(r);
+      const float zr = warp_sum(z * r);
+      const float beta = (cg && zr_prev > 0.f) ? fmaxf(zr / zr_prev, 0.f) : 0.f;
+      float p = __fmaf_rn(beta, p_prev, -z);
+      float ptr = warp_sum(p * r);
+      if (!(ptr < 0.f) && beta != 0.f) {  // lost descent: restart from -z
+        p = -z;
+        ptr = -zr;
+      }
       const float amax = warp_max(fabsf(ah));
       if (!(ptr < 0.f)) {
         const float pm = warp_max(fabsf(p));
@@ -703,6 +740,9 @@ struct WarpSolver {
       const float smax = warp_max(fabsf(dp));
       prev_small = precise && (smax <= kStepTol * amax) && (dfm <= kForceTol * fmax);
       prev_bits = act_bits;
+      cg = precise && !crossed;
+      p_prev = p;
+      zr_prev = zr;
       precise = precise || !crossed;
     }
   }
@@ -715,6 +755,7 @@ struct WarpSolver {
     wh = chol_solve(gj);
     wl = 0.f;
     float* Lm = Lam();
+    float* Lml = Lamlo();
     float lam_prev[MT];
 #pragma unroll
     for (int t = 0; t < MT; ++t) lam_prev[t] = 0.f;
@@ -732,8 +773,14 @@ struct WarpSolver {
       for (int t = 0; t < MT; ++t) {
         if (32 * t < m) {
           const bool on = (act_bits >> t) & 1u;
-          const float lam = on ? D_r[t] * __fadd_rn(s[t], c[t]) : 0.f;
-          if (row_valid(t)) Lm[lane + 32 * t] = lam;
+          const float uh = __fadd_rn(s[t], c[t]);
+          const float ul = __fsub_rn(c[t], __fsub_rn(uh, s[t]));
+          float lam = 0.f, lamlo = 0.f;
+          if (on) scale_pair(D_r[t], uh, ul, lam, lamlo);
+          if (row_valid(t)) {
+            Lm[lane + 32 * t] = lam;
+            Lml[lane + 32 * t] = lamlo;
+          }
           lmax = fmaxf(lmax, fabsf(lam));
           dl = fmaxf(dl, fabsf(lam - lam_prev[t]));
           lam_prev[t] = lam;
@@ -750,7 +797,7 @@ struct WarpSolver {
       }
       // rho = g - M w - J^T lambda (compensated)
       float js, jc, ms, mc;
-      jt_active(Lm, js, jc);
+      jt_active(Lm, Lml, js, jc);
       m_times(vh, vl, ms, mc);
       float t1, e1, t2, e2;
       two_sum(gj, -ms, t1, e1);

@@ -288,6 +288,7 @@ class FusedPlan:
                 "buckets": [{"nv_bucket": info.nv_bucket[i], "rows_per_lane": info.rows_per_lane[i],
                              "instances": info.instances[i],
                              "warps_per_block": info.warps_per_block[i],
+                             "kernel": "cta" if info.cta[i] else "warp",
                              "tuned_ms": round(float(info.tuned_ms[i]), 4)} for i in range(k)]}
 
     def close(self):

@@ -4,9 +4,13 @@ the same seeded inputs, compare instance by instance.
 Tolerances (per instance, per output array, relative to the oracle's
 infinity norm):  a <= 1e-4;  dqfrc, daref, dJ <= 1e-3;  active sets
 bit-identical on non-degenerate instances.  An instance is degenerate when a
-row sits on the cone boundary at the oracle's solution:
-|jar_i| < DEG_MARGIN * (sum_k |J_ik a_k| + |aref_i|); there the active set and
-the adjoint are not defined (the derivative is local to a fixed contact set).
+row sits on the cone boundary at the oracle's solution, measured on the scale
+that decides its side: an inactive row with
+jar_i < DEG_MARGIN * (sum_k |J_ik a_k| + |aref_i|), or an active row whose
+force |f_i| = D_i |jar_i| < FORCE_MARGIN * max_k |f_k| (stiff active rows
+have |jar| = |f| / D far below |J a| without being near the boundary).  There
+the active set and the adjoint are not defined (the derivative is local to a
+fixed contact set), so only a is compared.
 """
 from __future__ import annotations
 
@@ -18,6 +22,7 @@ import oracle
 A_TOL = 1e-4
 G_TOL = 1e-3
 DEG_MARGIN = 1e-6
+FORCE_MARGIN = 1e-5
 
 
 def rel(x, y):
@@ -74,10 +79,18 @@ def valid(w, out, key, masks=None):
 
 
 def compare(w, gpu, ref, idx, check_act=True):
-    """Per-instance comparison; returns a summary dict (fails nothing)."""
+    """Per-instance comparison; returns a summary dict (fails nothing).
+
+    Active sets must agree on every row that is not on the boundary (see the
+    module docstring).  An instance whose active sets agree on all rows gets
+    the full check (a and every gradient); one whose sets differ only on
+    boundary rows (a legitimate flip: the derivative is not defined there)
+    gets the a check and is counted in ``flipped``.
+    """
     worst = dict(a=0.0, dqfrc=0.0, daref=0.0, dJ=0.0)
     bad = []
     degenerate = 0
+    flipped = 0
     act_mismatch = []
     for b in idx:
         e = w.inst[b]
@@ -89,18 +102,36 @@ def compare(w, gpu, ref, idx, check_act=True):
         a_ref = ref["a"][ov:ov + nv]
         jar = p["J"].astype(np.float64) @ a_ref - p["aref"]
         scale = np.abs(p["J"].astype(np.float64)) @ np.abs(a_ref) + np.abs(p["aref"])
-        deg = bool(m) and bool(np.any(np.abs(jar) < DEG_MARGIN * scale))
-        if deg:
-            # a* is continuous across the boundary, so it is still checked
-            degenerate += 1
-            ea = rel(gpu["a"][ov:ov + nv], a_ref)
-            worst["a"] = max(worst["a"], ea)
+        f = p["D"].astype(np.float64) * np.minimum(jar, 0.0)
+        fmax = np.max(np.abs(f)) if m else 0.0
+        near = np.where(jar < 0, np.abs(f) < FORCE_MARGIN * fmax,
+                        jar < DEG_MARGIN * scale) if m else np.zeros(0, bool)
+        degenerate += bool(np.any(near))
+        ea = rel(gpu["a"][ov:ov + nv], a_ref)
+        worst["a"] = max(worst["a"], ea)
+        same = True
+        if check_act and m:
+            act_ref = ref["act"][orr:orr + m].astype(bool)
+            if "act" in gpu:
+                act_gpu = gpu["act"][orr:orr + m].astype(bool)
+            else:
+                # daref is zero exactly on inactive rows (an active row with
+                # J w = 0 exactly does not occur with continuous random data)
+                act_gpu = gpu["daref"][orr:orr + m] != 0
+            diff = act_gpu != act_ref
+            if np.any(diff & ~near):
+                act_mismatch.append(int(b))
+                bad.append((int(b), dict(a=ea, act="mismatch off the boundary"),
+                            int(gpu["status"][b]), int(gpu["iters"][b])))
+                continue
+            same = not np.any(diff)
+        if not same:
+            flipped += 1
             if ea > A_TOL or gpu["status"][b] != 0:
-                bad.append((int(b), dict(a=ea), int(gpu["status"][b]),
-                            int(gpu["iters"][b])))
+                bad.append((int(b), dict(a=ea), int(gpu["status"][b]), int(gpu["iters"][b])))
             continue
         errs = dict(
-            a=rel(gpu["a"][ov:ov + nv], a_ref),
+            a=ea,
             dqfrc=rel(gpu["dqfrc"][ov:ov + nv], ref["dqfrc"][ov:ov + nv]),
             daref=rel(gpu["daref"][orr:orr + m], ref["daref"][orr:orr + m]) if m else 0.0,
             dJ=rel(gpu["dJ"][oJ:oJ + m * nv], ref["dJ"][oJ:oJ + m * nv]) if m else 0.0,
@@ -109,19 +140,7 @@ def compare(w, gpu, ref, idx, check_act=True):
             worst[k] = max(worst[k], v)
         ok = (errs["a"] <= A_TOL and errs["dqfrc"] <= G_TOL and errs["daref"] <= G_TOL
               and errs["dJ"] <= G_TOL and gpu["status"][b] == 0)
-        if check_act and m:
-            act_ref = ref["act"][orr:orr + m].astype(bool)
-            if "act" in gpu:
-                act_gpu = gpu["act"][orr:orr + m].astype(bool)
-            else:
-                act_gpu = gpu["daref"][orr:orr + m] != 0
-                # daref is zero exactly on inactive rows; an active row with
-                # J w = 0 exactly would read as inactive, which random data
-                # never produces.
-            if not np.array_equal(act_gpu, act_ref):
-                act_mismatch.append(int(b))
-                ok = False
         if not ok:
             bad.append((int(b), errs, int(gpu["status"][b]), int(gpu["iters"][b])))
-    return dict(worst=worst, bad=bad, degenerate=degenerate, act_mismatch=act_mismatch,
-                checked=len(idx))
+    return dict(worst=worst, bad=bad, degenerate=degenerate, flipped=flipped,
+                act_mismatch=act_mismatch, checked=len(idx))

@@ -75,9 +75,12 @@ def _fused(lib, b, o, ws_bytes=256, ws=0x20000):
 def test_host_validation_codes(lib):
     assert _fused(lib, _batch(n=-1), _opts()) == _lib.CS_EINVAL
     assert _fused(lib, _batch(n=0), _opts()) == _lib.CS_OK        # no-op, no CUDA
-    assert _fused(lib, _batch(nv_max=33), _opts()) == _lib.CS_EUNSUPPORTED
+    assert _fused(lib, _batch(nv_max=129), _opts()) == _lib.CS_EUNSUPPORTED
+    # fits the CTA kernel's shared memory only up to about 45k words
+    assert _fused(lib, _batch(nv_max=128, m_max=1024), _opts()) == _lib.CS_EUNSUPPORTED
+    assert b"shared memory" in lib.cs_last_error()
     assert _fused(lib, _batch(nv_max=0), _opts()) == _lib.CS_EUNSUPPORTED
-    assert _fused(lib, _batch(m_max=257), _opts()) == _lib.CS_EUNSUPPORTED
+    assert _fused(lib, _batch(m_max=1025), _opts()) == _lib.CS_EUNSUPPORTED
     assert _fused(lib, _batch(M=None), _opts()) == _lib.CS_EINVAL
     assert _fused(lib, _batch(J=None), _opts()) == _lib.CS_EINVAL
     assert _fused(lib, _batch(total_J=-1), _opts()) == _lib.CS_EINVAL
