@@ -167,6 +167,102 @@ def cpu_baseline(w, max_instances=None, threads=None):
                       f"{threads} threads, {dt:.2f} s wall"}
 
 
+def _serve_pool(n_requests, rate, seed, pool_per_class=2048):
+    """Arrival times and a pool of request data per nv class (requests of a
+    class cycle through its pool; data drawn like the serving workload)."""
+    from paper_2607_24959_b300 import workloads as W
+    t, nv, nc = W.serve_stream(n_requests=n_requests, rate=rate, seed=seed)
+    pools = {}
+    for k, v in enumerate(sorted(set(nv.tolist()))):
+        sel = np.flatnonzero(nv == v)
+        P = int(min(pool_per_class, max(1, sel.size)))
+        w = W.generate(f"serve-nv{v}", P, int(v), nc[sel[:P]], seed=seed * 7 + k,
+                       cond=1e4 if v >= 96 else 1e3)
+        pools[int(v)] = [{kk: np.ascontiguousarray(x) for kk, x in w.instance(b).items()}
+                         for b in range(P)]
+    reqs = []
+    counters = {v: 0 for v in pools}
+    for i in range(n_requests):
+        v = int(nv[i])
+        reqs.append(pools[v][counters[v] % len(pools[v])])
+        counters[v] += 1
+    return t, reqs
+
+
+def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 << 30):
+    """Replay the arrivals against a server through the bulk C calls; latency
+    = completion - scheduled arrival (so any lag of the client counts too)."""
+    import ctypes
+    from paper_2607_24959_b300 import _lib, serve
+    n = len(reqs)
+    srv = serve.Server(arena_bytes=arena_bytes, streams=streams if policy != "fixed" else 1,
+                       max_batch=8192, policy=policy, fixed_batch=fixed_batch)
+    carr = serve.Server.make_requests(reqs)
+    tickets = (ctypes.c_uint64 * n)()
+    results = (_lib.CsResult * n)()
+    done = (ctypes.c_int32 * n)()
+    submitted = [0]
+    t0 = time.monotonic() + 0.05
+
+    def producer():
+        k = 0
+        while k < n:
+            now = time.monotonic() - t0
+            k1 = int(np.searchsorted(t_arr, now, side="right"))
+            if k1 > k:
+                got = srv.submit_batch(carr, k, k1, tickets)
+                k += got
+                submitted[0] = k
+            else:
+                dt = t_arr[k] - now
+                if dt > 2e-4:
+                    time.sleep(dt - 1e-4)
+        if policy == "fixed":
+            srv.flush()
+
+    th = threading.Thread(target=producer, daemon=True)
+    th.start()
+    lo = 0
+    deadline = time.monotonic() + 120.0 + float(t_arr[-1])
+    while lo < n:
+        hi = submitted[0]
+        if hi > lo:
+            srv.poll_batch(tickets, lo, hi, results, done)
+            while lo < hi and done[lo] == 1:
+                lo += 1
+            if any(done[i] < 0 for i in range(lo, hi)):
+                srv.close()
+                raise RuntimeError("serving lost a ticket")
+        if time.monotonic() > deadline:
+            srv.close()
+            raise RuntimeError(f"serving did not finish: {lo} of {n} collected")
+        time.sleep(1e-4)
+    th.join(timeout=10.0)
+    st = srv.stats()
+    srv.close()
+    t_done = np.array([results[i].t_done for i in range(n)])
+    status = np.array([results[i].status for i in range(n)])
+    lat = t_done - (t0 + np.asarray(t_arr))
+    span = t_done.max() - (t0 + t_arr[0])
+    return {"requests": n, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3), "solves_per_s": n / span,
+            "ok": int(np.sum(status == 0)), "batches": int(st["batches"]),
+            "mean_batch": st["batched_requests"] / max(st["batches"], 1),
+            "max_inflight": int(st["max_inflight"])}
+
+
+def run_serve(args):
+    """Serving stream (Poisson arrivals, nv in {3,9,18,96}, nc in 0..64):
+    continuous batching next to fixed-size launches of the same requests."""
+    t_arr, reqs = _serve_pool(args.serve_requests, args.serve_rate, 1005)
+    cont = serve_run(t_arr, reqs, "continuous")
+    fixed = serve_run(t_arr, reqs, "fixed", fixed_batch=args.serve_fixed_batch)
+    return {"requests": args.serve_requests, "rate_per_s": args.serve_rate,
+            "mix": "nv {3,9,18,96} p {.3,.3,.3,.1}, nc U{0..64}, fwd + adjoint each",
+            "continuous": cont, f"fixed_{args.serve_fixed_batch}": fixed}
+
+
 def run_reference(args):
     ws_, rank = _dist()
     if rank != 0:
@@ -300,6 +396,10 @@ def run_gpu(args):
             "iters_mean": float(iters.mean()), "iters_max": int(iters.max())}
     if e2e:
         line["e2e"] = e2e
+    if not args.no_serve and world == 1:
+        del plan, out, batch
+        torch.cuda.empty_cache()
+        line["serve"] = run_serve(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, max_instances=args.cpu_sample)
     print(json.dumps(line), flush=True)
@@ -375,6 +475,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=32768)
     ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-rate", type=float, default=50000.0)
+    ap.add_argument("--serve-fixed-batch", type=int, default=1024)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -70,6 +70,9 @@ extern "C" {
 #define CS_ST_BADSHAPE 4   /* nv/m outside the supported range, or offsets
                               outside the batch totals */
 #define CS_ST_NOPROGRESS 5 /* the Newton direction was not a descent one */
+#define CS_ST_FAILED 6     /* serving: the request's batch failed to launch
+                              or transfer (the error is counted in
+                              cs_serve_stats.failed_launches) */
 
 /* One instance of a ragged batch (40 bytes).  Offsets are in elements. */
 typedef struct cs_inst {
@@ -247,6 +250,94 @@ void cs_plan_destroy(cs_plan* plan);
  * such text and returns the number of entries taken. */
 int cs_autotune_cache_dump(char* buf, size_t len);
 int cs_autotune_cache_load(const char* text);
+
+/* ---- serving: continuous batching ------------------------------------ */
+
+#define CS_SERVE_CONTINUOUS 0 /* admit queued requests whenever a slot frees */
+#define CS_SERVE_FIXED 1      /* launch only batches of fixed_batch requests */
+
+/* Server configuration.  The device arena (arena_bytes) is split evenly over
+ * `streams` slots; each slot holds one batch in flight (inputs, outputs,
+ * tables), so a batch admits requests while they fit its slot's bytes
+ * (admission by device memory) and up to max_batch of them.  Several slots
+ * in flight on their own streams let later batches overlap earlier ones on
+ * the device.  Under CS_SERVE_CONTINUOUS a batch holds one kernel kind
+ * (instances one warp solves, or instances one CTA solves), taken in arrival
+ * order within the kind.  tol / max_iter as in cs_options.  max_queue bounds the host
+ * queue (0 = 2^20). */
+typedef struct cs_serve_config {
+  size_t arena_bytes;  /* >= 1 MiB per stream */
+  int32_t streams;     /* 1..16 */
+  int32_t max_batch;   /* >= 1 */
+  int32_t policy;      /* CS_SERVE_CONTINUOUS or CS_SERVE_FIXED */
+  int32_t fixed_batch; /* batch size of CS_SERVE_FIXED */
+  float tol;
+  int32_t max_iter;
+  int32_t max_queue;
+  int32_t reserved;
+} cs_serve_config;
+
+/* One request: a forward solve followed by the IFT adjoint for g.  All
+ * pointers are HOST memory, read during cs_serve_submit only (the data are
+ * copied).  Layouts as for one instance of a batch (row-major M, J). */
+typedef struct cs_request {
+  int32_t nv, m;
+  const float *M, *J, *qfrc, *aref, *D, *g;
+} cs_request;
+
+/* Result of a request.  The caller provides the host output buffers (nv,
+ * nv, m, m*nv floats; any may be NULL to skip it).  Times are seconds of one
+ * steady clock: submission, launch of its batch, completion seen by the
+ * server. */
+typedef struct cs_result {
+  float *a, *dqfrc, *daref, *dJ;
+  int32_t status, iters;
+  double t_submit, t_start, t_done;
+} cs_result;
+
+typedef struct cs_serve_stats {
+  int64_t submitted, completed, batches, batched_requests, queued;
+  int32_t max_inflight;    /* most batches on the GPU at once */
+  int32_t failed_launches;
+} cs_serve_stats;
+
+typedef struct cs_server cs_server; /* opaque, owned by the library */
+
+/* Create a server on the current device: allocates the arena and pinned
+ * staging, starts the scheduler thread.  CS_EINVAL / CS_ENOMEM on failure. */
+int cs_serve_create(const cs_serve_config* cfg, cs_server** out);
+
+/* Queue a request (its data are copied); *ticket identifies it.  Returns
+ * CS_EUNSUPPORTED for sizes no kernel or slot can take, CS_EBUSY when the
+ * queue is full.  Never blocks on the GPU. */
+int cs_serve_submit(cs_server* srv, const cs_request* req, uint64_t* ticket);
+
+/* CS_PENDING while the request is queued or on the GPU; CS_OK once done
+ * (outputs copied to res, the ticket is then retired); CS_ENOTFOUND for an
+ * unknown or retired ticket.  Never blocks. */
+int cs_serve_poll(cs_server* srv, uint64_t ticket, cs_result* res);
+
+/* Bulk forms for high-rate clients.  submit_batch queues reqs[0..n) in
+ * order and returns how many were queued (n, or fewer if one failed; a
+ * negative code if the first failed).  poll_batch polls each ticket whose
+ * done[i] is not already 1 (done is in/out, start it at 0) and sets done[i] =
+ * 1 (result in res[i], ticket retired), 0 (pending) or -1 (unknown); it
+ * returns the number completed in this call. */
+int cs_serve_submit_batch(cs_server* srv, int32_t n, const cs_request* reqs,
+                          uint64_t* tickets);
+int cs_serve_poll_batch(cs_server* srv, int32_t n, const uint64_t* tickets,
+                        cs_result* res, int32_t* done);
+
+/* Drop a request that is still queued (CS_EBUSY once it is on the GPU). */
+int cs_serve_cancel(cs_server* srv, uint64_t ticket);
+
+/* CS_SERVE_FIXED: release the queued requests as a partial batch. */
+int cs_serve_flush(cs_server* srv);
+
+int cs_serve_get_stats(cs_server* srv, cs_serve_stats* stats);
+
+/* Stop admitting, wait for the batches in flight, free everything. */
+void cs_serve_destroy(cs_server* srv);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,7 @@ CS_PENDING = 1
 
 ST_OK, ST_MAXITER, ST_CHOLFAIL, ST_NONFINITE, ST_BADSHAPE, ST_NOPROGRESS = range(6)
 STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "CHOLFAIL", 3: "NONFINITE",
-                4: "BADSHAPE", 5: "NOPROGRESS"}
+                4: "BADSHAPE", 5: "NOPROGRESS", 6: "FAILED"}
 
 
 class CsBatch(ctypes.Structure):
@@ -60,6 +60,32 @@ class CsPlanInfo(ctypes.Structure):
 
 CS_PLAN_AUTOTUNE = 1
 CS_PLAN_GRAPH = 2
+ST_FAILED = 6
+CS_SERVE_CONTINUOUS = 0
+CS_SERVE_FIXED = 1
+
+
+class CsServeConfig(ctypes.Structure):
+    _fields_ = [("arena_bytes", c_size_t), ("streams", c_int32), ("max_batch", c_int32),
+                ("policy", c_int32), ("fixed_batch", c_int32), ("tol", c_float),
+                ("max_iter", c_int32), ("max_queue", c_int32), ("reserved", c_int32)]
+
+
+class CsRequest(ctypes.Structure):
+    _fields_ = [("nv", c_int32), ("m", c_int32), ("M", c_void_p), ("J", c_void_p),
+                ("qfrc", c_void_p), ("aref", c_void_p), ("D", c_void_p), ("g", c_void_p)]
+
+
+class CsResult(ctypes.Structure):
+    _fields_ = [("a", c_void_p), ("dqfrc", c_void_p), ("daref", c_void_p), ("dJ", c_void_p),
+                ("status", c_int32), ("iters", c_int32), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class CsServeStats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("batches", c_int64),
+                ("batched_requests", c_int64), ("queued", c_int64),
+                ("max_inflight", c_int32), ("failed_launches", c_int32)]
 
 # name -> (restype, argtypes)
 _SIGS = {
@@ -88,6 +114,18 @@ _SIGS = {
     "cs_solve_fused_static": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
                                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                              c_void_p, c_void_p, c_void_p, c_void_p]),
+    "cs_serve_create": (ctypes.c_int, [ctypes.POINTER(CsServeConfig), ctypes.POINTER(c_void_p)]),
+    "cs_serve_submit": (ctypes.c_int, [c_void_p, ctypes.POINTER(CsRequest),
+                                       ctypes.POINTER(ctypes.c_uint64)]),
+    "cs_serve_poll": (ctypes.c_int, [c_void_p, ctypes.c_uint64, ctypes.POINTER(CsResult)]),
+    "cs_serve_cancel": (ctypes.c_int, [c_void_p, ctypes.c_uint64]),
+    "cs_serve_submit_batch": (ctypes.c_int, [c_void_p, c_int32, ctypes.POINTER(CsRequest),
+                                             ctypes.POINTER(ctypes.c_uint64)]),
+    "cs_serve_poll_batch": (ctypes.c_int, [c_void_p, c_int32, ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(CsResult), ctypes.POINTER(c_int32)]),
+    "cs_serve_flush": (ctypes.c_int, [c_void_p]),
+    "cs_serve_get_stats": (ctypes.c_int, [c_void_p, ctypes.POINTER(CsServeStats)]),
+    "cs_serve_destroy": (None, [c_void_p]),
 }
 
 STATIC_MAX_INSTANCES = 1 << 20

@@ -113,3 +113,19 @@ def test_python_layer_fails_loudly_without_library(tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
     finally:
         _lib._lib = saved
+
+
+def test_serve_argument_checks_without_gpu(lib):
+    h = ctypes.c_void_p(None)
+    assert lib.cs_serve_create(None, ctypes.byref(h)) == _lib.CS_EINVAL
+    c = _lib.CsServeConfig()
+    c.arena_bytes, c.streams, c.max_batch, c.policy, c.max_iter = 1 << 30, 0, 16, 0, 50
+    assert lib.cs_serve_create(ctypes.byref(c), ctypes.byref(h)) == _lib.CS_EINVAL
+    c.streams = 4
+    c.arena_bytes = 1 << 20                     # < 1 MiB per stream
+    assert lib.cs_serve_create(ctypes.byref(c), ctypes.byref(h)) == _lib.CS_EINVAL
+    c.arena_bytes, c.policy, c.fixed_batch = 1 << 30, 1, 0
+    assert lib.cs_serve_create(ctypes.byref(c), ctypes.byref(h)) == _lib.CS_EINVAL
+    t = ctypes.c_uint64(0)
+    assert lib.cs_serve_submit(None, None, ctypes.byref(t)) == _lib.CS_EINVAL
+    assert lib.cs_serve_poll(None, 1, None) == _lib.CS_EINVAL
