@@ -314,3 +314,122 @@ def autotune_cache_dump() -> str:
 
 def autotune_cache_load(text: str) -> int:
     return int(_lib.load().cs_autotune_cache_load(text.encode()))
+
+
+class HostPipeline:
+    """Fused solve of a host-resident batch with copies and compute overlapped.
+
+    The batch (pinned host arrays in the packed layout) is cut into
+    ``chunks`` contiguous instance ranges; their blocks are contiguous in
+    every packed array, so each chunk is one slice per array.  Per step and
+    chunk: the upload stream copies the chunk's inputs (instance table
+    included) into full-size device arrays at the same offsets, the compute
+    stream runs the chunk's plan (its own bucket kernels and CUDA graph), the
+    download stream copies the chunk's outputs back.  Uploads of chunk c+1,
+    the solve of chunk c and the download of chunk c-1 overlap.  Events make
+    a chunk's buffers safe to reuse across steps.
+    """
+
+    def __init__(self, w, chunks=8, device="cuda", tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
+                 autotune=False):
+        dev = torch.device(device)
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        self.w = w
+        self.h_in = dict(inst=pin(np.ascontiguousarray(w.inst).view(np.uint8)), M=pin(w.M),
+                         J=pin(w.J), qfrc=pin(w.qfrc), aref=pin(w.aref), D=pin(w.D), g=pin(w.g))
+        self.d_in = {k: torch.empty_like(v, device=dev) for k, v in self.h_in.items()}
+        full = DeviceBatch(self.d_in["inst"], self.d_in["M"], self.d_in["J"], self.d_in["qfrc"],
+                           self.d_in["aref"], self.d_in["D"], w.n, max(w.nv_max, 1), w.m_max,
+                           np.ascontiguousarray(w.inst))
+        self.out = alloc_fused(full)
+        self.h_out = dict(a=torch.empty_like(self.out.a, device="cpu").pin_memory(),
+                          dqfrc=torch.empty_like(self.out.dqfrc, device="cpu").pin_memory(),
+                          daref=torch.empty_like(self.out.daref, device="cpu").pin_memory(),
+                          dJ=torch.empty_like(self.out.dJ, device="cpu").pin_memory(),
+                          status=torch.empty_like(self.out.status, device="cpu").pin_memory(),
+                          iters=torch.empty_like(self.out.iters, device="cpu").pin_memory())
+        n = w.n
+        bounds = np.linspace(0, n, min(chunks, max(n, 1)) + 1).astype(int)
+        inst = w.inst
+        self.chunks = []
+        for c0, c1 in zip(bounds[:-1], bounds[1:]):
+            if c1 <= c0:
+                continue
+            e0, e1 = inst[c0], inst[c1 - 1]
+            sl = dict(
+                inst=(c0 * 40, c1 * 40),
+                M=(int(e0["off_M"]), int(e1["off_M"]) + int(e1["nv"]) ** 2),
+                J=(int(e0["off_J"]), int(e1["off_J"]) + int(e1["m"]) * int(e1["nv"])),
+                v=(int(e0["off_v"]), int(e1["off_v"]) + int(e1["nv"])),
+                r=(int(e0["off_r"]), int(e1["off_r"]) + int(e1["m"])))
+            part = DeviceBatch(self.d_in["inst"][c0 * 40:c1 * 40], full.M, full.J, full.qfrc,
+                               full.aref, full.D, int(c1 - c0),
+                               max(1, int(inst["nv"][c0:c1].max())), int(inst["m"][c0:c1].max()),
+                               np.ascontiguousarray(inst[c0:c1]))
+            self.chunks.append(dict(range=(int(c0), int(c1)), sl=sl, batch=part))
+        self.s_in = torch.cuda.Stream(device=dev)
+        self.s_comp = torch.cuda.Stream(device=dev)
+        self.s_out = torch.cuda.Stream(device=dev)
+        # plans read the inputs already uploaded: upload once before planning
+        for k in self.d_in:
+            self.d_in[k].copy_(self.h_in[k])
+        torch.cuda.synchronize()
+        with torch.cuda.stream(self.s_comp):
+            for ch in self.chunks:
+                c0, c1 = ch["range"]
+                # per-instance outputs (status, iters) are indexed by the
+                # instance's position in its chunk
+                o = FusedOut(self.out.a, self.out.dqfrc, self.out.daref, self.out.dJ,
+                             self.out.status[c0:c1], self.out.iters[c0:c1], self.out.workspace)
+                ch["plan"] = FusedPlan(ch["batch"], self.d_in["g"], tol=tol, max_iter=max_iter,
+                                       autotune=autotune, graph=True, out=o)
+        torch.cuda.synchronize()
+        mk = lambda: torch.cuda.Event()
+        for ch in self.chunks:
+            ch["ev_in"], ch["ev_comp"], ch["ev_out"] = mk(), mk(), mk()
+            ch["ev_comp"].record(self.s_comp)
+            ch["ev_out"].record(self.s_out)
+
+    def _copy(self, dst, src, lo, hi):
+        if hi > lo:
+            dst[lo:hi].copy_(src[lo:hi], non_blocking=True)
+
+    def step(self):
+        """Enqueue one pipelined pass (host inputs -> solve -> host outputs)."""
+        for ch in self.chunks:
+            sl = ch["sl"]
+            with torch.cuda.stream(self.s_in):
+                self.s_in.wait_event(ch["ev_comp"])       # inputs no longer read
+                self._copy(self.d_in["inst"], self.h_in["inst"], *sl["inst"])
+                self._copy(self.d_in["M"], self.h_in["M"], *sl["M"])
+                self._copy(self.d_in["J"], self.h_in["J"], *sl["J"])
+                for k in ("qfrc", "g"):
+                    self._copy(self.d_in[k], self.h_in[k], *sl["v"])
+                for k in ("aref", "D"):
+                    self._copy(self.d_in[k], self.h_in[k], *sl["r"])
+                ch["ev_in"].record(self.s_in)
+            with torch.cuda.stream(self.s_comp):
+                self.s_comp.wait_event(ch["ev_in"])
+                self.s_comp.wait_event(ch["ev_out"])      # outputs already read back
+                ch["plan"].launch()
+                ch["ev_comp"].record(self.s_comp)
+            with torch.cuda.stream(self.s_out):
+                self.s_out.wait_event(ch["ev_comp"])
+                c0, c1 = ch["range"]
+                self._copy(self.h_out["a"], self.out.a, *sl["v"])
+                self._copy(self.h_out["dqfrc"], self.out.dqfrc, *sl["v"])
+                self._copy(self.h_out["daref"], self.out.daref, *sl["r"])
+                self._copy(self.h_out["dJ"], self.out.dJ, *sl["J"])
+                self._copy(self.h_out["status"], self.out.status, c0, c1)
+                self._copy(self.h_out["iters"], self.out.iters, c0, c1)
+                ch["ev_out"].record(self.s_out)
+
+    def bytes_per_step(self):
+        h2d = sum(v.numel() * v.element_size() for v in self.h_in.values())
+        d2h = sum(v.numel() * v.element_size() for v in self.h_out.values())
+        return h2d, d2h
+
+    def close(self):
+        torch.cuda.synchronize()
+        for ch in self.chunks:
+            ch["plan"].close()

@@ -210,3 +210,18 @@ def test_iteration_cap_status(cuda_device):
     st = out.status.cpu().numpy()[:w.n]
     it = out.iters.cpu().numpy()[:w.n]
     assert np.all(it <= 1) and np.any(st == 1) and set(np.unique(st)) <= {0, 1}
+
+
+def test_host_pipeline_matches_device_path(cuda_device):
+    w = W.quadruped(n=3000, seed=71)
+    pipe = solver.HostPipeline(w, chunks=5, device=cuda_device)
+    for _ in range(2):
+        pipe.step()
+    torch.cuda.synchronize()
+    got = {k: v.numpy() for k, v in pipe.h_out.items()}
+    pipe.close()
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    ref = parity.run_gpu_fused(batch, w)
+    masks = parity.valid_mask(w)
+    for k in ("a", "dqfrc", "daref", "dJ", "status", "iters"):
+        assert np.array_equal(parity.valid(w, got, k, masks), parity.valid(w, ref, k, masks)), k
