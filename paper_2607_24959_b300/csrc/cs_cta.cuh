@@ -48,8 +48,14 @@ struct CtaGeo {
     g.oIdx = g.oLamlo + g.mcap;
     g.oVec = g.oIdx + g.mcap;
     g.oScr = g.oVec + 13 * g.nvcap;
-    g.oRed = g.oScr + 16 * kCtaThreads;  // split-K partials
-    g.words = g.oRed + 8 * kCtaWarps + 8;
+    // split-K partials: 2 floats per thread for the transposed products, and
+    // 16 per (block, row group) for the Newton matrix when it is split
+    const int nb = g.nvcap >> 2, nbl = nb * (nb + 1) / 2;
+    const int R = nbl >= kCtaThreads ? 1 : (kCtaThreads / nbl < 16 ? kCtaThreads / nbl : 16);
+    const int scr = R > 1 && 16 * nbl * R > 2 * kCtaThreads ? 16 * nbl * R : 2 * kCtaThreads;
+    g.oRed = g.oScr + scr;
+    g.words = g.oRed + 8 * kCtaWarps + 8;  // block sums use [0, 2 warps); the
+                                            // factor's pivot flag [4 warps + 7]
     return g;
   }
   __host__ __device__ size_t bytes() const { return ((size_t)words * 4 + 127) & ~(size_t)127; }
@@ -180,80 +186,189 @@ struct CtaSolver {
   }
 
   // ------------------------------------------------------------- Cholesky
-  // Right-looking, in place on the lower rows of Ls() (the padded rows are
-  // identity).  Returns false on a non-positive pivot.
+  // Blocked right-looking Cholesky, in place on the lower rows of Ls() (the
+  // padded rows are identity), panels of 32 columns:
+  //  1. the diagonal block by warp 0, left-looking (lane l = row kb + l);
+  //  2. the rows below it by forward substitution against that block, four
+  //     threads per row splitting each inner product;
+  //  3. the trailing matrix updated by all threads in 2x2 register blocks.
+  // Three barriers per panel.  Returns false on a non-positive pivot.
   __device__ __forceinline__ bool factor() {
     float* L = Ls();
     float* dv = V(C_DINV);
     const int nc = geo.nvcap, MS = geo.MS;
     bool ok = true;
 #pragma unroll 1
-    for (int k = 0; k < nc; ++k) {
-      const float d = L[k * MS + k];
-      ok = ok && (d > 0.f) && (d < CUDART_INF_F);
-      const float rs = rsqrtf(d);
-      __syncthreads();
-      if (tid == 0) {
-        const float lkk = d * rs;
-        L[k * MS + k] = lkk;
-        dv[k] = 1.0f / lkk;
+    for (int kb = 0; kb < nc; kb += 32) {
+      const int bs = min(32, nc - kb);
+      if (warp == 0) {
+        const int row = kb + min(lane, bs - 1);
+        const float* Lr = L + row * MS + kb;
+#pragma unroll 1
+        for (int k = 0; k < bs; ++k) {
+          const float* Lk = L + (kb + k) * MS + kb;
+          float a0 = Lr[k], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+          int i = 0;
+#pragma unroll 1
+          for (; i + 3 < k; i += 4) {
+            const float x0 = Lr[i], x1 = Lr[i + 1], x2 = Lr[i + 2], x3 = Lr[i + 3];
+            const float y0 = Lk[i], y1 = Lk[i + 1], y2 = Lk[i + 2], y3 = Lk[i + 3];
+            a0 = __fmaf_rn(-x0, y0, a0);
+            a1 = __fmaf_rn(-x1, y1, a1);
+            a2 = __fmaf_rn(-x2, y2, a2);
+            a3 = __fmaf_rn(-x3, y3, a3);
+          }
+#pragma unroll 1
+          for (; i < k; ++i) a0 = __fmaf_rn(-Lr[i], Lk[i], a0);
+          const float acc = (a0 + a1) + (a2 + a3);
+          const float d = __shfl_sync(kFull, acc, k);
+          ok = ok && (d > 0.f) && (d < CUDART_INF_F);
+          const float rs = rsqrtf(d);
+          __syncwarp();
+          if (lane == k) {
+            const float lkk = d * rs;
+            L[(kb + k) * MS + kb + k] = lkk;
+            dv[kb + k] = 1.0f / lkk;
+          } else if (lane > k && lane < bs) {
+            L[row * MS + kb + k] = acc * rs;
+          }
+          __syncwarp();
+        }
+        if (lane == 0) Red()[4 * kCtaWarps + 7] = ok ? 1.f : 0.f;
       }
-      for (int j = k + 1 + tid; j < nc; j += kCtaThreads) L[j * MS + k] *= rs;
       __syncthreads();
-      // trailing update, 16 x 16 thread tiles over (i, j), k < j <= i
-      const int ty = tid >> 4, tx = tid & 15;
-      for (int i = k + 1 + ty; i < nc; i += 16) {
-        const float lik = L[i * MS + k];
-        for (int j = k + 1 + tx; j <= i; j += 16) L[i * MS + j] = __fmaf_rn(-lik, L[j * MS + k], L[i * MS + j]);
+      const int r0 = kb + bs, nrows = nc - r0;
+      if (nrows > 0) {
+        const int q = tid & 3;
+#pragma unroll 1
+        for (int base = 0; base < nrows; base += kCtaThreads / 4) {
+          const int r = base + (tid >> 2);
+          const bool active = r < nrows;
+          const int i = r0 + min(r, nrows - 1);
+          float* Li = L + i * MS + kb;
+#pragma unroll 1
+          for (int c = 0; c < bs; ++c) {
+            const float* Lc = L + (kb + c) * MS + kb;
+            float part = 0.f;
+#pragma unroll 1
+            for (int pp = q; pp < c; pp += 4) part = __fmaf_rn(Li[pp], Lc[pp], part);
+            part += __shfl_xor_sync(kFull, part, 1);
+            part += __shfl_xor_sync(kFull, part, 2);
+            if (active && q == 0) Li[c] = (Li[c] - part) * dv[kb + c];
+            __syncwarp();
+          }
+        }
+      }
+      __syncthreads();
+      if (nrows > 0) {
+        const int nb2 = (nrows + 1) >> 1;
+        const int nblk = nb2 * (nb2 + 1) / 2;
+#pragma unroll 1
+        for (int w = tid; w < nblk; w += kCtaThreads) {
+          int bi = (int)((sqrtf(8.f * (float)w + 1.f) - 1.f) * 0.5f);
+          while (bi * (bi + 1) / 2 > w) --bi;
+          while ((bi + 1) * (bi + 2) / 2 <= w) ++bi;
+          const int bj = w - bi * (bi + 1) / 2;
+          const int i0 = r0 + 2 * bi, j0 = r0 + 2 * bj;
+          const int i1 = min(i0 + 1, nc - 1), j1 = min(j0 + 1, nc - 1);
+          const float* A0 = L + i0 * MS + kb;
+          const float* A1 = L + i1 * MS + kb;
+          const float* B0 = L + j0 * MS + kb;
+          const float* B1 = L + j1 * MS + kb;
+          float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
+#pragma unroll 4
+          for (int pp = 0; pp < bs; ++pp) {
+            const float a0 = A0[pp], a1 = A1[pp], b0 = B0[pp], b1 = B1[pp];
+            c00 = __fmaf_rn(a0, b0, c00);
+            c01 = __fmaf_rn(a0, b1, c01);
+            c10 = __fmaf_rn(a1, b0, c10);
+            c11 = __fmaf_rn(a1, b1, c11);
+          }
+          L[i0 * MS + j0] -= c00;
+          if (j0 + 1 <= i0 && j0 + 1 < nc) L[i0 * MS + j0 + 1] -= c01;
+          if (i0 + 1 < nc) {
+            L[(i0 + 1) * MS + j0] -= c10;
+            if (j0 + 1 <= i0 + 1 && j0 + 1 < nc) L[(i0 + 1) * MS + j0 + 1] -= c11;
+          }
+        }
       }
       __syncthreads();
     }
-    return ok;
+    const bool all_ok = Red()[4 * kCtaWarps + 7] != 0.f;  // warp 0's running flag
+    __syncthreads();
+    return all_ok;
   }
 
-  // x (in shared vector slot `slot`, nvcap entries) <- (L L^T)^-1 x.  Warp 0
-  // does the work with the rows spread over its lanes (row j = lane + 32 u);
-  // the other warps wait at the closing barrier.
+  // x (shared vector slot `slot`, nvcap entries) <- (L L^T)^-1 x, blocked by
+  // 32 rows: warp 0 solves each diagonal block with shuffles (lane = row);
+  // the coupling to the other blocks is a matrix-vector product spread over
+  // all threads.
   __device__ __forceinline__ void chol_solve(int slot) {
-    if (warp == 0) {
-      const float* L = Ls();
-      const float* dv = V(C_DINV);
-      float* X = V(slot);
-      const int nc = geo.nvcap, MS = geo.MS;
-      float x[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) x[u] = (lane + 32 * u < nc) ? X[lane + 32 * u] : 0.f;
+    const float* L = Ls();
+    const float* dv = V(C_DINV);
+    float* X = V(slot);
+    const int nc = geo.nvcap, MS = geo.MS;
+    // forward: L y = x
 #pragma unroll 1
-      for (int k = 0; k < nc; ++k) {
-        const int ku = k >> 5, kl = k & 31;
-        float own = (ku == 0) ? x[0] : (ku == 1) ? x[1] : (ku == 2) ? x[2] : x[3];
-        const float yk = __shfl_sync(kFull, own, kl) * dv[k];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = lane + 32 * u;
-          const float l = L[min(j, nc - 1) * MS + k];
-          const float upd = __fmaf_rn(-l, yk, x[u]);
-          x[u] = (j == k) ? yk : ((j > k && j < nc) ? upd : x[u]);
-        }
-      }
+    for (int kb = 0; kb < nc; kb += 32) {
+      const int bs = min(32, nc - kb);
+      if (warp == 0) {
+        float x = (lane < bs) ? X[kb + lane] : 0.f;
+        const float* Lr = L + (kb + min(lane, bs - 1)) * MS + kb;
 #pragma unroll 1
-      for (int k = nc - 1; k >= 0; --k) {
-        const int ku = k >> 5, kl = k & 31;
-        float own = (ku == 0) ? x[0] : (ku == 1) ? x[1] : (ku == 2) ? x[2] : x[3];
-        const float zk = __shfl_sync(kFull, own, kl) * dv[k];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = lane + 32 * u;
-          const float l = L[k * MS + min(j, nc - 1)];
-          const float upd = __fmaf_rn(-l, zk, x[u]);
-          x[u] = (j == k) ? zk : ((j < k) ? upd : x[u]);
+        for (int k = 0; k < bs; ++k) {
+          const float yk = __shfl_sync(kFull, x, k) * dv[kb + k];
+          const float upd = __fmaf_rn(-Lr[k], yk, x);
+          x = (lane == k) ? yk : ((lane > k && lane < bs) ? upd : x);
         }
+        if (lane < bs) X[kb + lane] = x;
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (lane + 32 * u < nc) X[lane + 32 * u] = x[u];
+      __syncthreads();
+      for (int i = kb + bs + tid; i < nc; i += kCtaThreads) {
+        const float* Li = L + i * MS + kb;
+        float t = 0.f, t2 = 0.f;
+        int k = 0;
+        for (; k + 1 < bs; k += 2) {
+          t = __fmaf_rn(Li[k], X[kb + k], t);
+          t2 = __fmaf_rn(Li[k + 1], X[kb + k + 1], t2);
+        }
+        if (k < bs) t = __fmaf_rn(Li[k], X[kb + k], t);
+        X[i] -= t + t2;
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    // backward: L^T x = y
+    const int last = ((nc - 1) / 32) * 32;
+#pragma unroll 1
+    for (int kb = last; kb >= 0; kb -= 32) {
+      const int bs = min(32, nc - kb);
+      const int below = kb + bs;
+      if (below < nc) {
+        // X[kb + l] -= sum_{j >= below} L[j][kb + l] X[j], 8 threads per row
+        const int l = tid >> 3, q = tid & 7;
+        const int i = kb + min(l, bs - 1);
+        float t = 0.f;
+        for (int j = below + q; j < nc; j += 8) t = __fmaf_rn(L[j * MS + i], X[j], t);
+        t += __shfl_xor_sync(kFull, t, 1);
+        t += __shfl_xor_sync(kFull, t, 2);
+        t += __shfl_xor_sync(kFull, t, 4);
+        __syncthreads();
+        if (q == 0 && l < bs) X[kb + l] -= t;
+        __syncthreads();
+      }
+      if (warp == 0) {
+        float x = (lane < bs) ? X[kb + lane] : 0.f;
+#pragma unroll 1
+        for (int k = bs - 1; k >= 0; --k) {
+          const float zk = __shfl_sync(kFull, x, k) * dv[kb + k];
+          const float lk = L[(kb + k) * MS + kb + min(lane, bs - 1)];
+          const float upd = __fmaf_rn(-lk, zk, x);
+          x = (lane == k) ? zk : ((lane < k) ? upd : x);
+        }
+        if (lane < bs) X[kb + lane] = x;
+      }
+      __syncthreads();
+    }
   }
 
   __device__ __forceinline__ bool factor_M() {
@@ -921,7 +1036,7 @@ struct CtaSolver {
 
 // One CTA per instance; CTAs claim instances dynamically or round-robin.
 template <int MTC, int MODE>
-__global__ void __launch_bounds__(kCtaThreads, 1) cta_solve_kernel(const __grid_constant__ Params P,
+__global__ void __launch_bounds__(kCtaThreads, MTC == 1 ? 2 : 1) cta_solve_kernel(const __grid_constant__ Params P,
                                                                  const CtaGeo geo) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int claim;
