@@ -11,6 +11,7 @@ ctypes.  Every function follows the paper's Section III:
 * ``solve_one``    Newton on the stationarity residual (Eqs. 6, 8, 9, 10) with
                    an exact line search and exact termination.
 * ``adjoint_one``  the transposed solve of Eq. 17 at the returned point.
+* ``adjoint_theta_one`` the same, adding the M and D terms of Eq. 17.
 * ``residual_one`` / ``objective_one``  Eq. 8 and Eq. 5 evaluated at a point.
 * ``solve_workload`` the same over a packed ragged batch, optionally on
                    several host threads (each thread runs the unchanged
@@ -77,8 +78,12 @@ def _load():
             lib.oracle_objective.restype = cd
             lib.oracle_batch.argtypes = [ci, ci, i32p, i32p, i64p, i64p, i64p,
                                          i64p, dp, dp, dp, dp, dp, dp, cd, ci,
-                                         dp, u8p, i32p, i32p, dp, dp, dp]
+                                         dp, u8p, i32p, i32p, dp, dp, dp, dp,
+                                         dp]
             lib.oracle_batch.restype = None
+            lib.oracle_adjoint_theta.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp,
+                                                 dp, dp, dp, dp, dp, dp, u8p]
+            lib.oracle_adjoint_theta.restype = ci
             lib.oracle_line_search.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp,
                                                dp]
             lib.oracle_line_search.restype = cd
@@ -133,6 +138,27 @@ def adjoint_one(M, J, qfrc, aref, D, a, g):
     return dq, dr[:m], dJ[:m * nv].reshape(m, nv), act[:m].astype(bool), int(st)
 
 
+def adjoint_theta_one(M, J, qfrc, aref, D, a, g):
+    """Returns (dqfrc, daref, dJ, dM, dD, act, status): Eq. 17 for every
+    parameter, dM being the derivative with respect to a symmetric M."""
+    lib = _load()
+    nv, m, arrs = _prob(M, J, qfrc, aref, D)
+    aa = _d(a)[0]
+    gp = _d(g)[1]
+    dq = np.zeros(nv)
+    dr = np.zeros(max(m, 1))
+    dJ = np.zeros(max(m * nv, 1))
+    dM = np.zeros(nv * nv)
+    dD = np.zeros(max(m, 1))
+    act = np.zeros(max(m, 1), np.uint8)
+    c = lambda x: x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = lib.oracle_adjoint_theta(
+        nv, m, *[p for _, p in arrs], c(aa), gp, c(dq), c(dr), c(dJ), c(dM),
+        c(dD), act.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return (dq, dr[:m], dJ[:m * nv].reshape(m, nv), dM.reshape(nv, nv), dD[:m],
+            act[:m].astype(bool), int(st))
+
+
 def residual_one(M, J, qfrc, aref, D, a):
     """Returns (r, f, act, scale) of Eq. 8 at the point a."""
     lib = _load()
@@ -169,13 +195,14 @@ def line_search_one(M, J, qfrc, aref, D, a, p):
 
 
 def solve_workload(w, idx=None, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
-                   adjoint=True, threads=1):
+                   adjoint=True, threads=1, theta=False):
     """Forward (+ adjoint with the workload's g) for a packed ragged batch.
 
     ``idx`` restricts the work to those instances (outputs of the others stay
     zero).  Returns a dict of packed float64 outputs (a, dqfrc, daref, dJ), the
     active set (uint8, packed like aref), status and iters (int32 per
-    instance).
+    instance).  With ``theta`` it adds dM (packed like M) and dD (packed like
+    D), the remaining parameter gradients of Eq. 17.
     """
     lib = _load()
     inst = w.inst
@@ -191,6 +218,8 @@ def solve_workload(w, idx=None, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
     dr = np.zeros(max(ar.size, 1))
     dJ = np.zeros(max(J.size, 1))
     act = np.zeros(max(ar.size, 1), np.uint8)
+    dM = np.zeros(max(M.size, 1)) if theta else None
+    dD = np.zeros(max(ar.size, 1)) if theta else None
     status = np.full(n, -1, np.int32)
     iters = np.zeros(n, np.int32)
     P = ctypes.POINTER
@@ -203,7 +232,8 @@ def solve_workload(w, idx=None, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
                          cd(M), cd(J), cd(q), cd(ar), cd(D),
                          cd(g) if adjoint else None, tol, max_iter, cd(a),
                          act.ctypes.data_as(P(ctypes.c_uint8)), ci32(status),
-                         ci32(iters), cd(dq), cd(dr), cd(dJ))
+                         ci32(iters), cd(dq), cd(dr), cd(dJ),
+                         cd(dM) if theta else None, cd(dD) if theta else None)
 
     if idx is None:
         ranges = []
@@ -233,5 +263,9 @@ def solve_workload(w, idx=None, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
             t.start()
         for t in ts:
             t.join()
-    return dict(a=a[:q.size], dqfrc=dq[:q.size], daref=dr[:ar.size],
-                dJ=dJ[:J.size], act=act[:ar.size], status=status, iters=iters)
+    out = dict(a=a[:q.size], dqfrc=dq[:q.size], daref=dr[:ar.size],
+               dJ=dJ[:J.size], act=act[:ar.size], status=status, iters=iters)
+    if theta:
+        out["dM"] = dM[:M.size]
+        out["dD"] = dD[:ar.size]
+    return out

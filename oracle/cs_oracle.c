@@ -270,10 +270,17 @@ done:
 /* Adjoint at the returned a (Eq. 17): H(a) w = g with the active set of a,
  * then dqfrc = w, daref = D_act . (J w), dJ = -(f w^T + daref a^T).
  * act (out, m) receives the active set used.  Returns 0 or OR_CHOLFAIL. */
-int oracle_adjoint(int nv, int m, const double *M, const double *J,
-                   const double *qfrc, const double *aref, const double *D,
-                   const double *a, const double *g, double *dqfrc,
-                   double *daref, double *dJ, uint8_t *act) {
+/* The remaining parameter terms of Eq. 17, for theta = M and theta = D:
+ *   dF/dM_kj = delta_kj-row a_j           -> dL/dM = -w a^T, read here as a
+ *     derivative with respect to a symmetric M (only the lower triangle is an
+ *     input), i.e. its symmetric part -(w a^T + a w^T) / 2;
+ *   dF/dD_i  = J_i^T min(jar_i, 0)       -> dL/dD_i = -(J w)_i min(jar_i, 0).
+ * dM (nv*nv, row-major) and dD (m) may each be NULL. */
+int oracle_adjoint_theta(int nv, int m, const double *M, const double *J,
+                         const double *qfrc, const double *aref,
+                         const double *D, const double *a, const double *g,
+                         double *dqfrc, double *daref, double *dJ, double *dM,
+                         double *dD, uint8_t *act) {
   if (nv < 1 || m < 0) return OR_BADSHAPE;
   problem P = {nv, m, M, J, qfrc, aref, D};
   double *w = (double *)calloc((size_t)(3 * m + 3 * nv + nv * nv + 8), sizeof(double));
@@ -294,9 +301,24 @@ int oracle_adjoint(int nv, int m, const double *M, const double *J,
   for (int i = 0; i < m; ++i)
     for (int k = 0; k < nv; ++k)
       dJ[i * nv + k] = -(f[i] * dqfrc[k] + daref[i] * a[k]);
+  if (dM)
+    for (int j = 0; j < nv; ++j)
+      for (int k = 0; k < nv; ++k)
+        dM[j * nv + k] = -0.5 * (dqfrc[j] * a[k] + a[j] * dqfrc[k]);
+  if (dD)
+    for (int i = 0; i < m; ++i) dD[i] = jar[i] < 0.0 ? -u[i] * jar[i] : 0.0;
 done:
   free(w);
   return status;
+}
+
+/* IFT adjoint of Eq. 17 for theta = (qfrc, aref, J) at the point a. */
+int oracle_adjoint(int nv, int m, const double *M, const double *J,
+                   const double *qfrc, const double *aref, const double *D,
+                   const double *a, const double *g, double *dqfrc,
+                   double *daref, double *dJ, uint8_t *act) {
+  return oracle_adjoint_theta(nv, m, M, J, qfrc, aref, D, a, g, dqfrc, daref,
+                              dJ, NULL, NULL, act);
 }
 
 /* Residual r(a), forces f and active set at a given a (for invariants). */
@@ -344,7 +366,8 @@ void oracle_batch(int lo, int hi, const int32_t *nv, const int32_t *m,
                   const double *J, const double *qfrc, const double *aref,
                   const double *D, const double *g, double tol, int max_iter,
                   double *a, uint8_t *act, int32_t *status, int32_t *iters,
-                  double *dqfrc, double *daref, double *dJ) {
+                  double *dqfrc, double *daref, double *dJ, double *dM,
+                  double *dD) {
   for (int b = lo; b < hi; ++b) {
     int it = 0;
     const double *Mb = M + off_M[b], *Jb = J + off_J[b];
@@ -354,10 +377,11 @@ void oracle_batch(int lo, int hi, const int32_t *nv, const int32_t *m,
     iters[b] = it;
     if (g && status[b] != OR_BADSHAPE && status[b] != OR_CHOLFAIL &&
         status[b] != OR_NONFINITE) {
-      int s2 = oracle_adjoint(nv[b], m[b], Mb, Jb, qfrc + off_v[b],
-                              aref + off_r[b], D + off_r[b], a + off_v[b],
-                              g + off_v[b], dqfrc + off_v[b], daref + off_r[b],
-                              dJ + off_J[b], act + off_r[b]);
+      int s2 = oracle_adjoint_theta(
+          nv[b], m[b], Mb, Jb, qfrc + off_v[b], aref + off_r[b], D + off_r[b],
+          a + off_v[b], g + off_v[b], dqfrc + off_v[b], daref + off_r[b],
+          dJ + off_J[b], dM ? dM + off_M[b] : NULL, dD ? dD + off_r[b] : NULL,
+          act + off_r[b]);
       if (s2) status[b] = s2;
     }
   }

@@ -10,7 +10,8 @@ determine independently of its code:
   of jar (strict convexity of Eq. 5 makes it unique);
 * the line search against a dense evaluation of phi (Eqs. 5, 10);
 * central finite differences of L = g^T a* with an epsilon sweep and the
-  active set held fixed (the paper's validation method, Section III-E);
+  active set held fixed (the paper's validation method, Section III-E), for
+  every parameter (qfrc, aref, J, and M, D through the full Eq. 17);
 * an independently written unrolled Newton solve differentiated by torch
   autograd, which must equal the IFT adjoint once the active set has settled
   (Eqs. 13-14) and differ from it when truncated early;
@@ -107,6 +108,58 @@ def test_single_row_closed_form():
         assert _rel(dq, w_cf) < 1e-9
         assert abs(dr[0] - dr_cf) <= 1e-8 * max(1.0, abs(dr_cf))
         assert _rel(dJ[0], dJ_cf) < 1e-8 or np.max(np.abs(dJ_cf)) == 0
+    assert 40 < n_active < 160
+
+
+def test_single_row_theta_closed_form():
+    """dL/dD and dL/dM of the one-row problem from the closed-form solution.
+
+    With c = j^T M^-1 j and jar0 = j^T a0 - aref < 0, the solution is
+    a*(D) = a0 - (D jar0 / (1 + D c)) M^-1 j, so dL/dD = g^T da*/dD =
+    -(g^T M^-1 j) jar0 / (1 + D c)^2.  For M, a*(M) is differentiated along a
+    symmetric direction E by the product rule on that same expression
+    (d M^-1 = -M^-1 E M^-1), giving a value to compare with <dM, E>."""
+    rng = np.random.default_rng(15)
+    n_active = 0
+    for trial in range(200):
+        nv = int(rng.integers(1, 8))
+        G = rng.standard_normal((nv, nv))
+        M = G @ G.T + 0.5 * np.eye(nv)
+        j = rng.standard_normal(nv)
+        aref = float(rng.standard_normal())
+        D = float(10 ** rng.uniform(2, 5))
+        qfrc = rng.standard_normal(nv)
+        g = rng.standard_normal(nv)
+        a, act, st, _ = oracle.solve_one(M, j[None, :], qfrc, [aref], [D])
+        assert st == 0
+        _, _, _, dM, dD, _, st2 = oracle.adjoint_theta_one(
+            M, j[None, :], qfrc, [aref], [D], a, g)
+        assert st2 == 0
+        Mi = np.linalg.inv(M)
+        a0 = Mi @ qfrc
+        mj = Mi @ j
+        c = j @ mj
+        jar0 = j @ a0 - aref
+        E = rng.standard_normal((nv, nv))
+        E = E + E.T
+        dMi = -Mi @ E @ Mi            # derivative of M^-1 along E
+        da0 = dMi @ qfrc
+        if jar0 < 0:
+            n_active += 1
+            dD_cf = -(g @ mj) * jar0 / (1.0 + D * c) ** 2
+            dmj = dMi @ j
+            dc = j @ dmj
+            djar0 = j @ da0
+            coef = D * jar0 / (1.0 + D * c)
+            dcoef = D * djar0 / (1.0 + D * c) - D * jar0 * D * dc / (1.0 + D * c) ** 2
+            da = da0 - dcoef * mj - coef * dmj
+        else:
+            dD_cf = 0.0
+            da = da0
+        assert abs(dD[0] - dD_cf) <= 1e-9 * max(abs(dD_cf), 1e-12) + 1e-15
+        dirn = g @ da
+        assert abs(np.sum(dM * E) - dirn) <= 1e-9 * max(1.0, abs(dirn))
+        assert np.allclose(dM, dM.T, rtol=0, atol=0)
     assert 40 < n_active < 160
 
 
@@ -282,6 +335,63 @@ def test_central_differences_with_epsilon_sweep():
     assert checked > 20 * skipped
 
 
+def test_theta_central_differences():
+    """dL/dM (symmetric perturbations M + h (E_jk + E_kj)) and dL/dD
+    (relative perturbations D_i e^{+-h}) against central FD of the forward
+    solve, the active set held fixed."""
+    skipped = checked = 0
+    for w in (W.tiny(8), W.franka(3)):
+        for b in range(w.n):
+            p = _f64(w.instance(b))
+            a, act, st, _ = _solve(p)
+            _, _, _, dM, dD, _, st2 = oracle.adjoint_theta_one(
+                p["M"], p["J"], p["qfrc"], p["aref"], p["D"], a, p["g"])
+            assert st2 == 0
+            nv = p["M"].shape[0]
+            cases = []
+            for j in range(nv):
+                for k in range(j + 1):
+                    E = np.zeros((nv, nv))
+                    E[j, k] += 1.0
+                    if j != k:
+                        E[k, j] += 1.0
+                    cases.append(("M", E, float(np.sum(dM * E))))
+            for i in range(p["D"].size):
+                cases.append(("D", i, float(p["D"][i] * dD[i])))
+            for key, dirn, expect in cases:
+                ests = {}
+                for h in (1e-4, 1e-5, 1e-6):
+                    vals = []
+                    for sgn in (1.0, -1.0):
+                        q = {k2: (v.copy() if isinstance(v, np.ndarray) else v)
+                             for k2, v in p.items()}
+                        if key == "M":
+                            q["M"] = q["M"] + sgn * h * dirn
+                        else:
+                            q["D"][dirn] *= np.exp(sgn * h)
+                        aa, aact, sst, _ = _solve(q)
+                        assert sst == 0
+                        if not np.array_equal(aact, act):
+                            vals = None
+                            break
+                        vals.append(float(q["g"] @ aa))
+                    if vals is None:
+                        ests = None
+                        break
+                    ests[h] = (vals[0] - vals[1]) / (2 * h)
+                if ests is None:
+                    skipped += 1
+                    continue
+                checked += 1
+                # h = 1e-4 balances truncation (h^2) against the solver's
+                # stopping tolerance divided by h
+                # (values are O(1e-5 .. 1); the absolute part covers the
+                # solver's stopping noise on the smallest of them)
+                assert abs(ests[1e-4] - ests[1e-5]) <= 1e-5 * abs(expect) + 1e-7
+                assert abs(ests[1e-4] - expect) <= 1e-6 * abs(expect) + 1e-8, (key, dirn)
+    assert checked > 20 * max(skipped, 1)
+
+
 # --------------------------------------------- unrolled Newton (torch autograd)
 
 def _unrolled_newton(M, J, q, ar, D, K):
@@ -338,17 +448,20 @@ def test_unrolled_newton_derivative_matches_ift():
     for b in range(w.n):
         p = _f64(w.instance(b))
         a, act, st, it = _solve(p)
-        dq, dr, dJ, _, _ = _adj(p, a)
+        dq, dr, dJ, dM, dD, _, _ = oracle.adjoint_theta_one(
+            p["M"], p["J"], p["qfrc"], p["aref"], p["D"], a, p["g"])
         for K, expect_equal in ((50, True), (1, False)):
             T = {k: torch.tensor(p[k], dtype=torch.float64, requires_grad=True)
-                 for k in ("qfrc", "aref", "J")}
-            Mt = torch.tensor(p["M"])
-            Dt = torch.tensor(p["D"])
+                 for k in ("qfrc", "aref", "J", "M", "D")}
             gt = torch.tensor(p["g"])
-            aK = _unrolled_newton(Mt, T["J"], T["qfrc"], T["aref"], Dt, K)
+            aK = _unrolled_newton(T["M"], T["J"], T["qfrc"], T["aref"], T["D"], K)
             (gt @ aK).backward()
+            # autograd sees M's nv^2 entries as independent; the gradient with
+            # respect to a symmetric M is the symmetric part of that one
+            gM = T["M"].grad.numpy()
             errs = [_rel(T["qfrc"].grad.numpy(), dq), _rel(T["aref"].grad.numpy(), dr),
-                    _rel(T["J"].grad.numpy(), dJ)]
+                    _rel(T["J"].grad.numpy(), dJ), _rel(0.5 * (gM + gM.T), dM),
+                    _rel(T["D"].grad.numpy(), dD)]
             if expect_equal:
                 assert _rel(aK.detach().numpy(), a) < 1e-11
                 assert max(errs) < 1e-8, errs
