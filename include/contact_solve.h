@@ -16,7 +16,9 @@
  *   and an exact line search on the piecewise-quadratic cost   (Eq. 10).
  *   Adjoint at the returned a, with F_a = H (symmetric)        (Eq. 17):
  *         H w = g,  dL/dqfrc = w,  dL/daref = D_act . (J w),
- *         dL/dJ = -(f w^T + (D_act . J w) a^T).
+ *         dL/dJ = -(f w^T + (D_act . J w) a^T),
+ *   and, from the *_theta entry points, dL/dM = -(w a^T + a w^T)/2 and
+ *         dL/dD = -(J w) . min(jar, 0).
  *
  * Conventions shared by every entry point:
  *  - All float data are IEEE binary32, row-major, packed per instance at the
@@ -149,6 +151,22 @@ int cs_solve_adjoint(const cs_batch* batch, const cs_options* opt,
                      const float* a, const cs_state* state, const float* g,
                      float* dqfrc, float* daref, float* dJ, void* stream);
 
+/* ---- the remaining parameters of Eq. 17: M and D ---------------------- */
+
+/* cs_solve_adjoint that also writes the gradients with respect to M and D
+ * (Eq. 17 with theta = M, D: F_M = (delta-row) a^T, F_D,i = J_i^T min(jar_i,0)):
+ *   dM (device, total_M, M's layout): -(w a^T + a w^T) / 2, the gradient with
+ *      respect to a symmetric M (the kernels read only M's lower triangle, so
+ *      M is a symmetric parameter; the symmetric part of -w a^T is its
+ *      gradient);
+ *   dD (device, total_r): -(J w)_i min(jar_i, 0), zero on inactive rows.
+ * Either may be NULL to skip it; with both NULL this is cs_solve_adjoint.
+ * Errors as for cs_solve_adjoint. */
+int cs_solve_adjoint_theta(const cs_batch* batch, const cs_options* opt,
+                           const float* a, const cs_state* state,
+                           const float* g, float* dqfrc, float* daref,
+                           float* dJ, float* dM, float* dD, void* stream);
+
 /* Bytes of device workspace cs_solve_fused needs for n instances. */
 size_t cs_fused_workspace_bytes(int32_t n);
 
@@ -164,6 +182,15 @@ int cs_solve_fused(const cs_batch* batch, const cs_options* opt,
                    float* dqfrc, float* daref, float* dJ, int32_t* status,
                    int32_t* iters, void* workspace, size_t workspace_bytes,
                    void* stream);
+
+/* cs_solve_fused that also writes dM and dD as cs_solve_adjoint_theta does
+ * (either may be NULL). */
+int cs_solve_fused_theta(const cs_batch* batch, const cs_options* opt,
+                         const float* g, const int32_t* order, float* a,
+                         float* dqfrc, float* daref, float* dJ, float* dM,
+                         float* dD, int32_t* status, int32_t* iters,
+                         void* workspace, size_t workspace_bytes,
+                         void* stream);
 
 /* ---- fused solve without any allocation ------------------------------- */
 
@@ -232,6 +259,15 @@ int cs_plan_create_fused(const cs_batch* batch, const cs_options* opt,
                          float* dqfrc, float* daref, float* dJ, int32_t* status,
                          int32_t* iters, int32_t flags, void* stream,
                          cs_plan** out);
+
+/* cs_plan_create_fused whose launches also write dM and dD as
+ * cs_solve_adjoint_theta does (either may be NULL). */
+int cs_plan_create_fused_theta(const cs_batch* batch, const cs_options* opt,
+                               const cs_inst* inst_host, const float* g,
+                               float* a, float* dqfrc, float* daref, float* dJ,
+                               float* dM, float* dD, int32_t* status,
+                               int32_t* iters, int32_t flags, void* stream,
+                               cs_plan** out);
 
 /* Enqueue the plan's work on `stream` (one graph launch, or the bucket
  * kernels in order).  Launches of one plan on different streams must not

@@ -97,7 +97,20 @@ _SIGS = {
     "cs_solve_adjoint": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
                                         c_void_p, ctypes.POINTER(CsState), c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p]),
+    "cs_solve_adjoint_theta": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
+                                              c_void_p, ctypes.POINTER(CsState), c_void_p,
+                                              c_void_p, c_void_p, c_void_p, c_void_p,
+                                              c_void_p, c_void_p]),
     "cs_fused_workspace_bytes": (c_size_t, [c_int32]),
+    "cs_solve_fused_theta": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
+                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_size_t, c_void_p]),
+    "cs_plan_create_fused_theta": (ctypes.c_int, [ctypes.POINTER(CsBatch),
+                                                  ctypes.POINTER(CsOptions), c_void_p, c_void_p,
+                                                  c_void_p, c_void_p, c_void_p, c_void_p,
+                                                  c_void_p, c_void_p, c_void_p, c_void_p,
+                                                  c_int32, c_void_p, ctypes.POINTER(c_void_p)]),
     "cs_solve_fused": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
                                       c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,

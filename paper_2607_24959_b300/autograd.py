@@ -4,8 +4,10 @@ adjoint of Eq. 17, never an unrolled solver trace.
 Forward runs ``cs_solve_fwd`` and keeps only the adjoint state (a*, a_lo, the
 active set and, by default, the Cholesky factor of H(a*)), whose size does not
 depend on the number of Newton iterations.  Backward runs
-``cs_solve_adjoint`` on grad_a and returns dL/dJ, dL/dqfrc and dL/daref.  M and
-D are treated as constants (their cotangents are not produced).
+``cs_solve_adjoint`` on grad_a and returns dL/dJ, dL/dqfrc and dL/daref; when
+M or D requires grad it runs ``cs_solve_adjoint_theta`` instead and also
+returns dL/dM (with respect to a symmetric M: -(w a^T + a w^T)/2) and dL/dD
+(-(J w) . min(jar, 0)), the remaining parameter terms of Eq. 17.
 
 With ``keep_factor=False`` the factor is not stored; the backward rebuilds it
 from the stored active set (less memory, one extra factorisation).
@@ -38,20 +40,27 @@ class ContactSolve(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_a):
         (a,) = ctx.saved_tensors
-        dq, dr, dJ = solver.solve_adjoint(ctx.batch, a, ctx.state,
-                                          grad_a.contiguous(), tol=ctx.tol,
-                                          max_iter=ctx.max_iter)
+        theta = ctx.needs_input_grad[1] or ctx.needs_input_grad[5]
+        res = solver.solve_adjoint(ctx.batch, a, ctx.state, grad_a.contiguous(),
+                                   tol=ctx.tol, max_iter=ctx.max_iter, theta=theta)
+        dq, dr, dJ = res[:3]
         b = ctx.batch
         dJ = dJ[:b.J.numel()].view_as(b.J) if b.J.numel() else torch.zeros_like(b.J)
         dr = dr[:b.aref.numel()].view_as(b.aref) if b.aref.numel() else torch.zeros_like(b.aref)
         dq = dq[:b.qfrc.numel()].view_as(b.qfrc)
-        return None, None, dJ, dq, dr, None, None, None, None
+        dM = dD = None
+        if theta:
+            dM = res[3][:b.M.numel()].view_as(b.M) if ctx.needs_input_grad[1] else None
+            if ctx.needs_input_grad[5]:
+                dD = (res[4][:b.D.numel()].view_as(b.D) if b.D.numel()
+                      else torch.zeros_like(b.D))
+        return None, dM, dJ, dq, dr, dD, None, None, None
 
 
 def contact_solve(batch: solver.DeviceBatch, M=None, J=None, qfrc=None, aref=None,
                   D=None, tol=solver.DEFAULT_TOL, max_iter=solver.DEFAULT_MAX_ITER,
                   keep_factor=True):
-    """a* for the batch; differentiable w.r.t. J, qfrc and aref."""
+    """a* for the batch; differentiable w.r.t. M, J, qfrc, aref and D."""
     return ContactSolve.apply(batch, batch.M if M is None else M,
                               batch.J if J is None else J,
                               batch.qfrc if qfrc is None else qfrc,

@@ -201,6 +201,13 @@ int cs_solve_fwd(const cs_batch* batch, const cs_options* opt, float* a, const c
 int cs_solve_adjoint(const cs_batch* batch, const cs_options* opt, const float* a,
                      const cs_state* st, const float* g, float* dqfrc, float* daref, float* dJ,
                      void* stream) {
+  return cs_solve_adjoint_theta(batch, opt, a, st, g, dqfrc, daref, dJ, nullptr, nullptr,
+                                stream);
+}
+
+int cs_solve_adjoint_theta(const cs_batch* batch, const cs_options* opt, const float* a,
+                           const cs_state* st, const float* g, float* dqfrc, float* daref,
+                           float* dJ, float* dM, float* dD, void* stream) {
   int rc = check_batch(batch, opt);
   if (rc != CS_OK || batch->n == 0) return rc;
   if (!a || !st || !st->a_lo || !st->status || !st->iters || !g || !dqfrc ||
@@ -217,6 +224,8 @@ int cs_solve_adjoint(const cs_batch* batch, const cs_options* opt, const float* 
   P.dqfrc = dqfrc;
   P.daref = daref;
   P.dJ = dJ;
+  P.dM = dM;
+  P.dD = batch->m_max > 0 ? dD : nullptr;
   LaunchCfg cfg;
   cfg.warps_per_block = opt->warps_per_block;
   cudaError_t e = launch_dispatch(csk::MODE_ADJ, batch->nv_max, batch->m_max, P, cfg,
@@ -233,6 +242,14 @@ int cs_solve_fused(const cs_batch* batch, const cs_options* opt, const float* g,
                    const int32_t* order, float* a, float* dqfrc, float* daref, float* dJ,
                    int32_t* status, int32_t* iters, void* workspace, size_t workspace_bytes,
                    void* stream) {
+  return cs_solve_fused_theta(batch, opt, g, order, a, dqfrc, daref, dJ, nullptr, nullptr,
+                              status, iters, workspace, workspace_bytes, stream);
+}
+
+int cs_solve_fused_theta(const cs_batch* batch, const cs_options* opt, const float* g,
+                         const int32_t* order, float* a, float* dqfrc, float* daref, float* dJ,
+                         float* dM, float* dD, int32_t* status, int32_t* iters,
+                         void* workspace, size_t workspace_bytes, void* stream) {
   int rc = check_batch(batch, opt);
   if (rc != CS_OK || batch->n == 0) return rc;
   if (!g || !a || !dqfrc || !status || !iters || (batch->m_max > 0 && (!daref || !dJ)))
@@ -247,6 +264,8 @@ int cs_solve_fused(const cs_batch* batch, const cs_options* opt, const float* g,
   P.dqfrc = dqfrc;
   P.daref = daref;
   P.dJ = dJ;
+  P.dM = dM;
+  P.dD = batch->m_max > 0 ? dD : nullptr;
   P.status = status;
   P.iters = iters;
   P.counter = reinterpret_cast<int32_t*>(workspace);

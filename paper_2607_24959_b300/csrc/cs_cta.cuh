@@ -906,12 +906,32 @@ struct CtaSolver {
       const int rr = q / nv, cc = q - rr * nv;
       dJ[q] = -__fmaf_rn(F[rr], wh[cc], Lm[rr] * ah[cc]);
     }
+    if (P.dD) {
+#pragma unroll
+      for (int u = 0; u < MTC; ++u)
+        if (row_valid(u)) {
+          const int i = row(u);
+          P.dD[e.off_r + i] = jar_r[u] < 0.f ? -__fdiv_rn(Lm[i] * jar_r[u], D_r[u]) : 0.f;
+        }
+    }
+    if (P.dM) {
+      float* dM = P.dM + e.off_M;
+#pragma unroll 1
+      for (int q = tid; q < nv * nv; q += kCtaThreads) {
+        const int rr = q / nv, cc = q - rr * nv;
+        dM[q] = -0.5f * __fmaf_rn(wh[rr], ah[cc], ah[rr] * wh[cc]);
+      }
+    }
   }
 
   __device__ __forceinline__ void zero_grads(const Params& P, const cs_inst& e) {
     for (int j = tid; j < nv; j += kCtaThreads) P.dqfrc[e.off_v + j] = 0.f;
     for (int i = tid; i < m; i += kCtaThreads) P.daref[e.off_r + i] = 0.f;
     for (int q = tid; q < m * nv; q += kCtaThreads) P.dJ[e.off_J + q] = 0.f;
+    if (P.dD)
+      for (int i = tid; i < m; i += kCtaThreads) P.dD[e.off_r + i] = 0.f;
+    if (P.dM)
+      for (int q = tid; q < nv * nv; q += kCtaThreads) P.dM[e.off_M + q] = 0.f;
   }
 
   __device__ __forceinline__ void load_factor(const float* Lp) {

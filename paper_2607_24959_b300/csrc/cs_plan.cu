@@ -180,6 +180,14 @@ int cs_plan_create_fused(const cs_batch* batch, const cs_options* opt, const cs_
                          const float* g, float* a, float* dqfrc, float* daref, float* dJ,
                          int32_t* status, int32_t* iters, int32_t flags, void* stream,
                          cs_plan** out) {
+  return cs_plan_create_fused_theta(batch, opt, inst_host, g, a, dqfrc, daref, dJ, nullptr,
+                                    nullptr, status, iters, flags, stream, out);
+}
+
+int cs_plan_create_fused_theta(const cs_batch* batch, const cs_options* opt,
+                               const cs_inst* inst_host, const float* g, float* a, float* dqfrc,
+                               float* daref, float* dJ, float* dM, float* dD, int32_t* status,
+                               int32_t* iters, int32_t flags, void* stream, cs_plan** out) {
   if (!out) return set_error(CS_EINVAL, "out must not be NULL");
   *out = nullptr;
   int rc = check_batch_shapes(batch, opt);
@@ -196,6 +204,8 @@ int cs_plan_create_fused(const cs_batch* batch, const cs_options* opt, const cs_
   p->base.dqfrc = dqfrc;
   p->base.daref = daref;
   p->base.dJ = dJ;
+  p->base.dM = dM;
+  p->base.dD = batch->m_max > 0 ? dD : nullptr;
   p->base.status = status;
   p->base.iters = iters;
   cudaStream_t s = (cudaStream_t)stream;

@@ -126,6 +126,7 @@ struct Params {
   int64_t total_M, total_J, total_v, total_r;
   float* a;                 // out (fwd, fused) / in (adjoint)
   float *dqfrc, *daref, *dJ;
+  float *dM, *dD;           // optional parameter gradients for M and D, or null
   float* a_lo;              // state
   uint8_t* act;             // state
   float* Lst;               // state factor (packed lower rows) or null
@@ -811,7 +812,9 @@ struct WarpSolver {
     __syncwarp();
   }
 
-  // Write dqfrc = w, daref = lambda, dJ = -(f w^T + lambda a^T).
+  // Write dqfrc = w, daref = lambda, dJ = -(f w^T + lambda a^T), and when
+  // asked for, dM = -(w a^T + a w^T) / 2 (M symmetric) and
+  // dD_i = -(J w)_i min(jar_i, 0) = -lambda_i jar_i / D_i on active rows.
   __device__ __forceinline__ void write_grads(const Params& P, const cs_inst& e, float wh) {
     if (lane < nv) P.dqfrc[e.off_v + lane] = wh;
     const float* Lm = Lam();
@@ -836,6 +839,24 @@ struct WarpSolver {
         cc = q - rr * nv;
       }
       dJ[q] = -__fmaf_rn(F[rr], vw[cc], Lm[rr] * va[cc]);
+    }
+    if (P.dD) {
+#pragma unroll
+      for (int t = 0; t < MT; ++t)
+        if (row_valid(t)) {
+          const bool on = (act_bits >> t) & 1u;
+          P.dD[e.off_r + lane + 32 * t] =
+              on ? -__fdiv_rn(Lm[lane + 32 * t] * jar_r[t], D_r[t]) : 0.f;
+        }
+    }
+    if (P.dM) {
+      float* dM = P.dM + e.off_M;
+      const int nn = nv * nv;
+#pragma unroll 1
+      for (int q = lane; q < nn; q += 32) {
+        const int rr = q / nv, cc = q - rr * nv;
+        dM[q] = -0.5f * __fmaf_rn(vw[rr], va[cc], va[rr] * vw[cc]);
+      }
     }
   }
 
@@ -871,6 +892,12 @@ struct WarpSolver {
     for (int i = lane; i < m; i += 32) P.daref[e.off_r + i] = 0.f;
 #pragma unroll 1
     for (int q = lane; q < m * nv; q += 32) P.dJ[e.off_J + q] = 0.f;
+    if (P.dD)
+#pragma unroll 1
+      for (int i = lane; i < m; i += 32) P.dD[e.off_r + i] = 0.f;
+    if (P.dM)
+#pragma unroll 1
+      for (int q = lane; q < nv * nv; q += 32) P.dM[e.off_M + q] = 0.f;
   }
 
   // ------------------------------------------------------------ drivers

@@ -151,19 +151,30 @@ def solve_fwd(batch: DeviceBatch, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
 
 
 def solve_adjoint(batch: DeviceBatch, a, state: State, g, tol=DEFAULT_TOL,
-                  max_iter=DEFAULT_MAX_ITER, warps_per_block=0, out=None):
-    """IFT adjoint at the forward state; returns (dqfrc, daref, dJ)."""
+                  max_iter=DEFAULT_MAX_ITER, warps_per_block=0, out=None, theta=False):
+    """IFT adjoint at the forward state; returns (dqfrc, daref, dJ), or with
+    ``theta`` (dqfrc, daref, dJ, dM, dD) from cs_solve_adjoint_theta (dM packed
+    like M, dD like D)."""
     lib = _lib.load()
     dev = batch.M.device
     if out is None:
         out = (torch.empty(max(batch.total_v, 1), dtype=torch.float32, device=dev),
                torch.empty(max(batch.total_r, 1), dtype=torch.float32, device=dev),
                torch.empty(max(batch.J.numel(), 1), dtype=torch.float32, device=dev))
-    dq, dr, dJ = out
+        if theta:
+            out = out + (torch.empty(max(batch.M.numel(), 1), dtype=torch.float32, device=dev),
+                         torch.empty(max(batch.total_r, 1), dtype=torch.float32, device=dev))
     b = batch.cstruct()
     o = options(tol, max_iter, state.keep_factor, warps_per_block)
     st = state.cstruct()
     g = g.contiguous()
+    if theta:
+        dq, dr, dJ, dM, dD = out
+        _lib.check(lib.cs_solve_adjoint_theta(
+            ctypes.byref(b), ctypes.byref(o), _ptr(a), ctypes.byref(st), _ptr(g), _ptr(dq),
+            _ptr(dr), _ptr(dJ), _ptr(dM), _ptr(dD), _stream()), "cs_solve_adjoint_theta")
+        return dq, dr, dJ, dM, dD
+    dq, dr, dJ = out[:3]
     _lib.check(lib.cs_solve_adjoint(ctypes.byref(b), ctypes.byref(o), _ptr(a),
                                     ctypes.byref(st), _ptr(g), _ptr(dq), _ptr(dr),
                                     _ptr(dJ), _stream()), "cs_solve_adjoint")
@@ -183,9 +194,11 @@ class FusedOut:
     status: torch.Tensor
     iters: torch.Tensor
     workspace: torch.Tensor
+    dM: torch.Tensor | None = None   # dL/dM (symmetric M), packed like M
+    dD: torch.Tensor | None = None   # dL/dD, packed like D
 
 
-def alloc_fused(batch: DeviceBatch) -> FusedOut:
+def alloc_fused(batch: DeviceBatch, theta: bool = False) -> FusedOut:
     dev = batch.M.device
     ws = torch.zeros(fused_workspace_bytes(batch.n), dtype=torch.uint8, device=dev)
     return FusedOut(
@@ -195,18 +208,32 @@ def alloc_fused(batch: DeviceBatch) -> FusedOut:
         dJ=torch.empty(max(batch.J.numel(), 1), dtype=torch.float32, device=dev),
         status=torch.empty(max(batch.n, 1), dtype=torch.int32, device=dev),
         iters=torch.empty(max(batch.n, 1), dtype=torch.int32, device=dev),
-        workspace=ws)
+        workspace=ws,
+        dM=(torch.empty(max(batch.M.numel(), 1), dtype=torch.float32, device=dev)
+            if theta else None),
+        dD=(torch.empty(max(batch.total_r, 1), dtype=torch.float32, device=dev)
+            if theta else None))
 
 
 def solve_fused(batch: DeviceBatch, g, order=None, tol=DEFAULT_TOL,
-                max_iter=DEFAULT_MAX_ITER, warps_per_block=0, out: FusedOut | None = None):
-    """Fused forward + adjoint in one persistent launch; returns FusedOut."""
+                max_iter=DEFAULT_MAX_ITER, warps_per_block=0, out: FusedOut | None = None,
+                theta: bool = False):
+    """Fused forward + adjoint in one persistent launch; returns FusedOut.
+    With ``theta`` (or an ``out`` holding dM/dD) the launch also writes dL/dM
+    and dL/dD (cs_solve_fused_theta)."""
     lib = _lib.load()
     if out is None:
-        out = alloc_fused(batch)
+        out = alloc_fused(batch, theta)
     b = batch.cstruct()
     o = options(tol, max_iter, True, warps_per_block)
     g = g.contiguous()
+    if out.dM is not None or out.dD is not None:
+        _lib.check(lib.cs_solve_fused_theta(
+            ctypes.byref(b), ctypes.byref(o), _ptr(g), _ptr(order), _ptr(out.a),
+            _ptr(out.dqfrc), _ptr(out.daref), _ptr(out.dJ), _ptr(out.dM), _ptr(out.dD),
+            _ptr(out.status), _ptr(out.iters), _ptr(out.workspace), out.workspace.numel(),
+            _stream()), "cs_solve_fused_theta")
+        return out
     _lib.check(lib.cs_solve_fused(
         ctypes.byref(b), ctypes.byref(o), _ptr(g), _ptr(order), _ptr(out.a),
         _ptr(out.dqfrc), _ptr(out.daref), _ptr(out.dJ), _ptr(out.status),
@@ -256,11 +283,12 @@ class FusedPlan:
     """
 
     def __init__(self, batch: DeviceBatch, g, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
-                 autotune=True, graph=True, warps_per_block=0, out: FusedOut | None = None):
+                 autotune=True, graph=True, warps_per_block=0, out: FusedOut | None = None,
+                 theta: bool = False):
         lib = _lib.load()
         self.batch = batch
         self.g = g.contiguous()
-        self.out = out if out is not None else alloc_fused(batch)
+        self.out = out if out is not None else alloc_fused(batch, theta)
         self._b = batch.cstruct()
         self._o = options(tol, max_iter, True, warps_per_block)
         self._inst_host = np.ascontiguousarray(batch.inst_host)
@@ -268,11 +296,19 @@ class FusedPlan:
                  (_lib.CS_PLAN_GRAPH if graph else 0))
         h = ctypes.c_void_p(None)
         o = self.out
-        _lib.check(lib.cs_plan_create_fused(
-            ctypes.byref(self._b), ctypes.byref(self._o),
-            self._inst_host.ctypes.data_as(ctypes.c_void_p), _ptr(self.g), _ptr(o.a),
-            _ptr(o.dqfrc), _ptr(o.daref), _ptr(o.dJ), _ptr(o.status), _ptr(o.iters), flags,
-            _stream(), ctypes.byref(h)), "cs_plan_create_fused")
+        if o.dM is not None or o.dD is not None:
+            _lib.check(lib.cs_plan_create_fused_theta(
+                ctypes.byref(self._b), ctypes.byref(self._o),
+                self._inst_host.ctypes.data_as(ctypes.c_void_p), _ptr(self.g), _ptr(o.a),
+                _ptr(o.dqfrc), _ptr(o.daref), _ptr(o.dJ), _ptr(o.dM), _ptr(o.dD),
+                _ptr(o.status), _ptr(o.iters), flags, _stream(), ctypes.byref(h)),
+                "cs_plan_create_fused_theta")
+        else:
+            _lib.check(lib.cs_plan_create_fused(
+                ctypes.byref(self._b), ctypes.byref(self._o),
+                self._inst_host.ctypes.data_as(ctypes.c_void_p), _ptr(self.g), _ptr(o.a),
+                _ptr(o.dqfrc), _ptr(o.daref), _ptr(o.dJ), _ptr(o.status), _ptr(o.iters),
+                flags, _stream(), ctypes.byref(h)), "cs_plan_create_fused")
         self._h = h
         self._lib = lib
 

@@ -2,7 +2,7 @@
 the same seeded inputs, compare instance by instance.
 
 Tolerances (per instance, per output array, relative to the oracle's
-infinity norm):  a <= 1e-4;  dqfrc, daref, dJ <= 1e-3;  active sets
+infinity norm):  a <= 1e-4;  dqfrc, daref, dJ (and dM, dD) <= 1e-3;  active sets
 bit-identical on non-degenerate instances.  An instance is degenerate when a
 row sits on the cone boundary at the oracle's solution, measured on the scale
 that decides its side: an inactive row with
@@ -34,26 +34,34 @@ def rel(x, y):
     return float(d / max(np.max(np.abs(y)), 1e-30))
 
 
-def run_gpu_fused(batch, w, **kw):
+def run_gpu_fused(batch, w, theta=False, **kw):
     from paper_2607_24959_b300 import solver
     g = torch.from_numpy(np.ascontiguousarray(w.g, np.float32)).to(batch.M.device)
-    out = solver.solve_fused(batch, g, **kw)
+    out = solver.solve_fused(batch, g, theta=theta, **kw)
     torch.cuda.synchronize()
-    return dict(a=out.a.cpu().numpy(), dqfrc=out.dqfrc.cpu().numpy(),
-                daref=out.daref.cpu().numpy(), dJ=out.dJ.cpu().numpy(),
-                status=out.status.cpu().numpy(), iters=out.iters.cpu().numpy())
+    res = dict(a=out.a.cpu().numpy(), dqfrc=out.dqfrc.cpu().numpy(),
+               daref=out.daref.cpu().numpy(), dJ=out.dJ.cpu().numpy(),
+               status=out.status.cpu().numpy(), iters=out.iters.cpu().numpy())
+    if theta:
+        res["dM"] = out.dM.cpu().numpy()
+        res["dD"] = out.dD.cpu().numpy()
+    return res
 
 
-def run_gpu_split(batch, w, keep_factor=True, **kw):
+def run_gpu_split(batch, w, keep_factor=True, theta=False, **kw):
     from paper_2607_24959_b300 import solver
     g = torch.from_numpy(np.ascontiguousarray(w.g, np.float32)).to(batch.M.device)
     a, st = solver.solve_fwd(batch, keep_factor=keep_factor, **kw)
-    dq, dr, dJ = solver.solve_adjoint(batch, a, st, g, **kw)
+    grads = solver.solve_adjoint(batch, a, st, g, theta=theta, **kw)
     torch.cuda.synchronize()
-    return dict(a=a.cpu().numpy(), dqfrc=dq.cpu().numpy(), daref=dr.cpu().numpy(),
-                dJ=dJ.cpu().numpy(), status=st.status.cpu().numpy(),
-                iters=st.iters.cpu().numpy(), act=st.act.cpu().numpy(),
-                a_lo=st.a_lo.cpu().numpy())
+    res = dict(a=a.cpu().numpy(), dqfrc=grads[0].cpu().numpy(),
+               daref=grads[1].cpu().numpy(), dJ=grads[2].cpu().numpy(),
+               status=st.status.cpu().numpy(), iters=st.iters.cpu().numpy(),
+               act=st.act.cpu().numpy(), a_lo=st.a_lo.cpu().numpy())
+    if theta:
+        res["dM"] = grads[3].cpu().numpy()
+        res["dD"] = grads[4].cpu().numpy()
+    return res
 
 
 def valid_mask(w):
@@ -61,12 +69,14 @@ def valid_mask(w):
     mv = np.zeros(w.qfrc.size, bool)
     mr = np.zeros(w.aref.size, bool)
     mJ = np.zeros(w.J.size, bool)
+    mM = np.zeros(w.M.size, bool)
     for e in w.inst:
         nv, m = int(e["nv"]), int(e["m"])
         mv[e["off_v"]:e["off_v"] + nv] = True
         mr[e["off_r"]:e["off_r"] + m] = True
         mJ[e["off_J"]:e["off_J"] + m * nv] = True
-    return dict(a=mv, dqfrc=mv, a_lo=mv, daref=mr, act=mr, dJ=mJ)
+        mM[e["off_M"]:e["off_M"] + nv * nv] = True
+    return dict(a=mv, dqfrc=mv, a_lo=mv, daref=mr, act=mr, dJ=mJ, dM=mM, dD=mr)
 
 
 def valid(w, out, key, masks=None):
@@ -87,7 +97,10 @@ def compare(w, gpu, ref, idx, check_act=True):
     boundary rows (a legitimate flip: the derivative is not defined there)
     gets the a check and is counted in ``flipped``.
     """
+    theta = "dM" in gpu and "dM" in ref
     worst = dict(a=0.0, dqfrc=0.0, daref=0.0, dJ=0.0)
+    if theta:
+        worst.update(dM=0.0, dD=0.0)
     bad = []
     degenerate = 0
     flipped = 0
@@ -96,6 +109,7 @@ def compare(w, gpu, ref, idx, check_act=True):
         e = w.inst[b]
         nv, m = int(e["nv"]), int(e["m"])
         ov, orr, oJ = int(e["off_v"]), int(e["off_r"]), int(e["off_J"])
+        oM = int(e["off_M"])
         if ref["status"][b] != 0:
             continue
         p = w.instance(b)
@@ -136,10 +150,13 @@ def compare(w, gpu, ref, idx, check_act=True):
             daref=rel(gpu["daref"][orr:orr + m], ref["daref"][orr:orr + m]) if m else 0.0,
             dJ=rel(gpu["dJ"][oJ:oJ + m * nv], ref["dJ"][oJ:oJ + m * nv]) if m else 0.0,
         )
+        if theta:
+            errs["dM"] = rel(gpu["dM"][oM:oM + nv * nv], ref["dM"][oM:oM + nv * nv])
+            errs["dD"] = rel(gpu["dD"][orr:orr + m], ref["dD"][orr:orr + m]) if m else 0.0
         for k, v in errs.items():
             worst[k] = max(worst[k], v)
-        ok = (errs["a"] <= A_TOL and errs["dqfrc"] <= G_TOL and errs["daref"] <= G_TOL
-              and errs["dJ"] <= G_TOL and gpu["status"][b] == 0)
+        ok = (errs["a"] <= A_TOL and all(v <= G_TOL for k, v in errs.items() if k != "a")
+              and gpu["status"][b] == 0)
         if not ok:
             bad.append((int(b), errs, int(gpu["status"][b]), int(gpu["iters"][b])))
     return dict(worst=worst, bad=bad, degenerate=degenerate, flipped=flipped,
