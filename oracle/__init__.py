@@ -12,6 +12,9 @@ ctypes.  Every function follows the paper's Section III:
                    an exact line search and exact termination.
 * ``adjoint_one``  the transposed solve of Eq. 17 at the returned point.
 * ``adjoint_theta_one`` the same, adding the M and D terms of Eq. 17.
+* ``unrolled_one`` / ``unrolled_workload``  the derivative through the
+                   executed trace of at most K Newton steps (the unrolled
+                   reverse-mode sensitivity the paper compares with IFT).
 * ``residual_one`` / ``objective_one``  Eq. 8 and Eq. 5 evaluated at a point.
 * ``solve_workload`` the same over a packed ragged batch, optionally on
                    several host threads (each thread runs the unchanged
@@ -84,6 +87,9 @@ def _load():
             lib.oracle_adjoint_theta.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp,
                                                  dp, dp, dp, dp, dp, dp, u8p]
             lib.oracle_adjoint_theta.restype = ci
+            lib.oracle_unrolled.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp, ci,
+                                            cd, dp, ip, dp, dp, dp, dp, dp]
+            lib.oracle_unrolled.restype = ci
             lib.oracle_line_search.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp,
                                                dp]
             lib.oracle_line_search.restype = cd
@@ -157,6 +163,69 @@ def adjoint_theta_one(M, J, qfrc, aref, D, a, g):
         c(dD), act.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
     return (dq, dr[:m], dJ[:m * nv].reshape(m, nv), dM.reshape(nv, nv), dD[:m],
             act[:m].astype(bool), int(st))
+
+
+def unrolled_one(M, J, qfrc, aref, D, g, K, tol=DEFAULT_TOL):
+    """Derivative of g^T a_K through the executed trace of at most K Newton
+    steps (unrolled reverse mode, Section III-E).  Returns a dict with a (the
+    returned a_K), steps, status and dqfrc, daref, dJ, dM (symmetric M), dD."""
+    lib = _load()
+    nv, m, arrs = _prob(M, J, qfrc, aref, D)
+    gp = _d(g)[1]
+    a = np.zeros(nv)
+    dq = np.zeros(nv)
+    dr = np.zeros(max(m, 1))
+    dJ = np.zeros(max(m * nv, 1))
+    dM = np.zeros(nv * nv)
+    dD = np.zeros(max(m, 1))
+    steps = ctypes.c_int(0)
+    c = lambda x: x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = lib.oracle_unrolled(nv, m, *[p for _, p in arrs], gp, int(K), float(tol),
+                             c(a), ctypes.byref(steps), c(dq), c(dr), c(dJ), c(dM),
+                             c(dD))
+    return dict(a=a, steps=int(steps.value), status=int(st), dqfrc=dq, daref=dr[:m],
+                dJ=dJ[:m * nv].reshape(m, nv), dM=dM.reshape(nv, nv), dD=dD[:m])
+
+
+def unrolled_workload(w, K, idx=None, tol=DEFAULT_TOL, threads=1):
+    """unrolled_one over a packed ragged batch (with the workload's g).
+    Returns packed float64 a, dqfrc, daref, dJ, dM, dD and per-instance
+    status and steps; instances outside ``idx`` stay zero."""
+    inst = w.inst
+    n = inst.shape[0]
+    out = dict(a=np.zeros(w.qfrc.size), dqfrc=np.zeros(w.qfrc.size),
+               daref=np.zeros(w.aref.size), dJ=np.zeros(w.J.size),
+               dM=np.zeros(w.M.size), dD=np.zeros(w.aref.size),
+               status=np.full(n, -1, np.int32), iters=np.zeros(n, np.int32))
+    todo = np.arange(n) if idx is None else np.asarray(idx).ravel()
+
+    def run(bs):
+        for b in bs:
+            e = inst[int(b)]
+            nv, m = int(e["nv"]), int(e["m"])
+            ov, orr, oJ, oM = (int(e[k]) for k in ("off_v", "off_r", "off_J", "off_M"))
+            p = w.instance(int(b))
+            res = unrolled_one(p["M"], p["J"], p["qfrc"], p["aref"], p["D"], p["g"], K,
+                               tol)
+            out["a"][ov:ov + nv] = res["a"]
+            out["dqfrc"][ov:ov + nv] = res["dqfrc"]
+            out["daref"][orr:orr + m] = res["daref"]
+            out["dD"][orr:orr + m] = res["dD"]
+            out["dJ"][oJ:oJ + m * nv] = res["dJ"].ravel()
+            out["dM"][oM:oM + nv * nv] = res["dM"].ravel()
+            out["status"][int(b)] = res["status"]
+            out["iters"][int(b)] = res["steps"]
+
+    if threads <= 1 or todo.size < 2:
+        run(todo)
+    else:
+        ts = [threading.Thread(target=run, args=(part,))
+              for part in np.array_split(todo, threads) if part.size]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+    return out
 
 
 def residual_one(M, J, qfrc, aref, D, a):

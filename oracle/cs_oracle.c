@@ -387,6 +387,228 @@ void oracle_batch(int lo, int hi, const int32_t *nv, const int32_t *m,
   }
 }
 
+/* ---- unrolled reverse-mode derivative (the paper's comparison) --------- */
+
+/* Derivative of L = g^T a_K through the executed trace of at most K Newton
+ * steps (the "unrolled AD" sensitivity of Section III-E, which the paper sets
+ * against the IFT adjoint of Eq. 17).
+ *
+ * Forward, in the order of oracle_solve: a_0 = M^-1 qfrc (Eq. 1); at step k,
+ * stop if ||r||_inf <= tol * scale (or k = K, or p^T r >= 0); otherwise
+ * S_k = {jar < 0}, H_k (Eq. 9), p_k = -H_k^-1 r_k, then either exact
+ * termination (the mask at a_k + p_k equals S_k: alpha_k = 1, T_k = S_k, and
+ * the loop ends after this step) or the exact line search (Eq. 10), which
+ * returns alpha_k = -c0/c1 on the segment whose rows T_k = {jar + alpha s <
+ * 0} are active, with
+ *   c0 = p^T (M a - qfrc) + sum_{T} D_i s_i jar_i,  c1 = p^T M p + sum_{T} D_i s_i^2,
+ *   s = J p.  Then a_{k+1} = a_k + alpha_k p_k.
+ * The trace keeps a_k, p_k, alpha_k, S_k and T_k; the masks are locally
+ * constant, so the derivative is that of the smooth map each step applies.
+ *
+ * Reverse (cotangents written xb), per step from the last:
+ *   alpha_b = ab . p,  pb = alpha ab,  a_k's cotangent starts at ab;
+ *   alpha = -c0/c1:   c0b = -alpha_b / c1,  c1b = -alpha_b alpha / c1;
+ *   c0, c1:  pb += c0b (M a - qfrc) + 2 c1b M p,  a_kb += c0b M p,
+ *            Mb += c0b p a^T + c1b p p^T,  qfrcb -= c0b p,
+ *            rows of T:  Db += c0b s jar + c1b s^2,  sb = c0b D jar + 2 c1b D s,
+ *                        jarb += c0b D s;
+ *   s = J p:          pb += J^T sb,  Jb += sb p^T;
+ *   p = -H^-1 r:      z = H^-1 pb,  rb = -z,  Hb = -z p^T;
+ *   H = M + J_S^T D_S J_S:  Mb += Hb,  rows of S: Jb_i -= D_i (s_i z + (J z)_i p),
+ *                        Db_i -= (J z)_i s_i;
+ *   r = M a - qfrc + J^T f:  a_kb -= M z,  Mb -= z a^T,  qfrcb += z,
+ *                        Jb_i -= f_i z,  fb = -J z;
+ *   f = D_S jar:      rows of S: Db += fb jar,  jarb += fb D;
+ *   jar = J a - aref: a_kb += J^T jarb,  Jb += jarb a^T,  arefb -= jarb.
+ * Finally a_0 = M^-1 qfrc: y = M^-1 ab, qfrcb += y, Mb -= y a_0^T.  M is a
+ * symmetric parameter (as in oracle_adjoint_theta): dM = (Mb + Mb^T) / 2.
+ *
+ * Outputs a (the returned a_K), *steps, and dqfrc, daref, dJ, dM, dD (any of
+ * the last five may be NULL).  Returns a status code as oracle_solve. */
+int oracle_unrolled(int nv, int m, const double *M, const double *J,
+                    const double *qfrc, const double *aref, const double *D,
+                    const double *g, int K, double tol, double *a, int *steps,
+                    double *dqfrc, double *daref, double *dJ, double *dM,
+                    double *dD) {
+  *steps = 0;
+  if (nv < 1 || m < 0 || K < 0) return OR_BADSHAPE;
+  problem P = {nv, m, M, J, qfrc, aref, D};
+  const size_t km = (size_t)(K > 0 ? K : 1) * (size_t)(m > 0 ? m : 1);
+  double *A = (double *)calloc((size_t)(K + 1) * nv, sizeof(double));
+  double *Pk = (double *)calloc((size_t)(K > 0 ? K : 1) * nv, sizeof(double));
+  double *alph = (double *)calloc((size_t)(K > 0 ? K : 1), sizeof(double));
+  uint8_t *Sk = (uint8_t *)calloc(km, 1), *Tk = (uint8_t *)calloc(km, 1);
+  size_t wd = (size_t)(10 * m + 12 * nv + 4 * nv * nv + 8);
+  double *w = (double *)calloc(wd, sizeof(double));
+  breakpoint *bp = (breakpoint *)calloc((size_t)m + 1, sizeof(breakpoint));
+  uint8_t *act = (uint8_t *)calloc((size_t)m + 1, 1);
+  double *jar = w, *f = jar + m, *s = f + m, *jar2 = s + m, *sb = jar2 + m;
+  double *jarb = sb + m, *Jz = jarb + m, *Db = Jz + m, *arb = Db + m;
+  double *Ma = arb + m, *Jtf = Ma + nv, *r = Jtf + nv, *p = r + nv;
+  double *Mp = p + nv, *ab = Mp + nv, *akb = ab + nv, *pb = akb + nv, *z = pb + nv;
+  double *qb = z + nv, *Maq = qb + nv, *y = Maq + nv;
+  double *H = y + nv, *Mb = H + nv * nv, *Jb = NULL;
+  int status = OR_MAXITER, n = 0;
+
+  /* ---- forward: a_0 = M^-1 qfrc, then at most K recorded Newton steps */
+  memcpy(H, M, sizeof(double) * nv * nv);
+  if (chol(nv, H)) { status = OR_CHOLFAIL; goto done; }
+  memcpy(A, qfrc, sizeof(double) * nv);
+  chol_solve(nv, H, A);
+  for (int k = 0;; ++k) {
+    double *ak = A + (size_t)k * nv;
+    double scale = residual(&P, ak, jar, act, f, Ma, Jtf, r);
+    double rn = inf_norm(nv, r);
+    if (!isfinite(rn) || !isfinite(scale)) { status = OR_NONFINITE; break; }
+    if (rn <= tol * scale) { status = OR_OK; break; }
+    if (k >= K) { status = OR_MAXITER; break; }
+    newton_matrix(&P, act, H);
+    if (chol(nv, H)) { status = OR_CHOLFAIL; break; }
+    for (int j = 0; j < nv; ++j) p[j] = -r[j];
+    chol_solve(nv, H, p);
+    double ptr = 0.0;
+    for (int j = 0; j < nv; ++j) ptr += p[j] * r[j];
+    if (!(ptr < 0.0)) { status = OR_NOPROGRESS; break; }
+    int same = 1;
+    for (int i = 0; i < m; ++i) {
+      double v = 0.0;
+      for (int q = 0; q < nv; ++q) v += J[i * nv + q] * (ak[q] + p[q]);
+      if ((v - aref[i] < 0.0) != (act[i] != 0)) same = 0;
+    }
+    double alpha = same ? 1.0 : line_search(&P, ak, p, jar, Ma, s, bp);
+    for (int i = 0; i < m; ++i) {
+      double si = 0.0;
+      for (int q = 0; q < nv; ++q) si += J[i * nv + q] * p[q];
+      Sk[(size_t)k * m + i] = act[i];
+      Tk[(size_t)k * m + i] = same ? act[i] : (jar[i] + alpha * si < 0.0);
+    }
+    memcpy(Pk + (size_t)k * nv, p, sizeof(double) * nv);
+    alph[k] = alpha;
+    for (int j = 0; j < nv; ++j) ak[nv + j] = ak[j] + alpha * p[j];
+    n = k + 1;
+    if (same) { status = OR_OK; break; }
+  }
+  *steps = n;
+  memcpy(a, A + (size_t)n * nv, sizeof(double) * nv);
+  if (status == OR_CHOLFAIL || status == OR_NONFINITE) goto done;
+
+  /* ---- reverse sweep over the recorded steps */
+  Jb = (double *)calloc((size_t)(m > 0 ? m : 1) * nv, sizeof(double));
+  memcpy(ab, g, sizeof(double) * nv);
+  for (int k = n - 1; k >= 0; --k) {
+    const double *ak = A + (size_t)k * nv, *pk = Pk + (size_t)k * nv;
+    const uint8_t *S = Sk + (size_t)k * m, *T = Tk + (size_t)k * m;
+    const double alpha = alph[k];
+    for (int i = 0; i < m; ++i) {
+      double u = 0.0, v = 0.0;
+      for (int q = 0; q < nv; ++q) {
+        u += J[i * nv + q] * ak[q];
+        v += J[i * nv + q] * pk[q];
+      }
+      jar[i] = u - aref[i];
+      s[i] = v;
+      f[i] = S[i] ? D[i] * jar[i] : 0.0;
+      sb[i] = 0.0;
+      jarb[i] = 0.0;
+    }
+    double c1 = 0.0, alpha_b = 0.0;
+    for (int j = 0; j < nv; ++j) {
+      double u = 0.0, v = 0.0;
+      for (int q = 0; q < nv; ++q) {
+        u += M[j * nv + q] * pk[q];
+        v += M[j * nv + q] * ak[q];
+      }
+      Mp[j] = u;
+      Maq[j] = v - qfrc[j];
+      c1 += pk[j] * u;
+      alpha_b += ab[j] * pk[j];
+    }
+    for (int i = 0; i < m; ++i)
+      if (T[i]) c1 += D[i] * s[i] * s[i];
+    const double c0b = -alpha_b / c1, c1b = -alpha_b * alpha / c1;
+    for (int j = 0; j < nv; ++j) {
+      pb[j] = alpha * ab[j] + c0b * Maq[j] + 2.0 * c1b * Mp[j];
+      akb[j] = ab[j] + c0b * Mp[j];
+      qb[j] -= c0b * pk[j];
+      for (int q = 0; q < nv; ++q)
+        Mb[j * nv + q] += c0b * pk[j] * ak[q] + c1b * pk[j] * pk[q];
+    }
+    for (int i = 0; i < m; ++i) {
+      if (!T[i]) continue;
+      Db[i] += c0b * s[i] * jar[i] + c1b * s[i] * s[i];
+      sb[i] = c0b * D[i] * jar[i] + 2.0 * c1b * D[i] * s[i];
+      jarb[i] += c0b * D[i] * s[i];
+    }
+    for (int i = 0; i < m; ++i)
+      for (int q = 0; q < nv; ++q) {
+        pb[q] += J[i * nv + q] * sb[i];
+        Jb[i * nv + q] += sb[i] * pk[q];
+      }
+    newton_matrix(&P, S, H);
+    if (chol(nv, H)) { status = OR_CHOLFAIL; goto done; }
+    memcpy(z, pb, sizeof(double) * nv);
+    chol_solve(nv, H, z);
+    for (int i = 0; i < m; ++i) {
+      double v = 0.0;
+      for (int q = 0; q < nv; ++q) v += J[i * nv + q] * z[q];
+      Jz[i] = v;
+    }
+    for (int j = 0; j < nv; ++j) {
+      double v = 0.0;
+      for (int q = 0; q < nv; ++q) v += M[j * nv + q] * z[q];
+      akb[j] -= v;
+      qb[j] += z[j];
+      for (int q = 0; q < nv; ++q) Mb[j * nv + q] -= z[j] * pk[q] + z[j] * ak[q];
+    }
+    for (int i = 0; i < m; ++i) {
+      for (int q = 0; q < nv; ++q) Jb[i * nv + q] -= f[i] * z[q];
+      if (!S[i]) continue;
+      for (int q = 0; q < nv; ++q)
+        Jb[i * nv + q] -= D[i] * (s[i] * z[q] + Jz[i] * pk[q]);
+      Db[i] -= Jz[i] * s[i];
+      const double fb = -Jz[i];
+      Db[i] += fb * jar[i];
+      jarb[i] += fb * D[i];
+    }
+    for (int i = 0; i < m; ++i) {
+      for (int q = 0; q < nv; ++q) {
+        akb[q] += J[i * nv + q] * jarb[i];
+        Jb[i * nv + q] += jarb[i] * ak[q];
+      }
+      arb[i] -= jarb[i];
+    }
+    memcpy(ab, akb, sizeof(double) * nv);
+  }
+  /* a_0 = M^-1 qfrc */
+  memcpy(H, M, sizeof(double) * nv * nv);
+  if (chol(nv, H)) { status = OR_CHOLFAIL; goto done; }
+  memcpy(y, ab, sizeof(double) * nv);
+  chol_solve(nv, H, y);
+  for (int j = 0; j < nv; ++j) {
+    qb[j] += y[j];
+    for (int q = 0; q < nv; ++q) Mb[j * nv + q] -= y[j] * A[q];
+  }
+  if (dqfrc) memcpy(dqfrc, qb, sizeof(double) * nv);
+  if (daref) memcpy(daref, arb, sizeof(double) * m);
+  if (dD) memcpy(dD, Db, sizeof(double) * m);
+  if (dJ) memcpy(dJ, Jb, sizeof(double) * m * nv);
+  if (dM)
+    for (int j = 0; j < nv; ++j)
+      for (int q = 0; q < nv; ++q)
+        dM[j * nv + q] = 0.5 * (Mb[j * nv + q] + Mb[q * nv + j]);
+done:
+  free(A);
+  free(Pk);
+  free(alph);
+  free(Sk);
+  free(Tk);
+  free(w);
+  free(bp);
+  free(act);
+  free(Jb);
+  return status;
+}
+
 /* The exact line search on its own, for pinning it: returns the minimiser of
  * phi(alpha) = L(a + alpha p) over alpha > 0. */
 double oracle_line_search(int nv, int m, const double *M, const double *J,

@@ -420,7 +420,7 @@ def _unrolled_newton(M, J, q, ar, D, K):
         s = J @ d
         # locate the segment of phi' holding its root with detached values,
         # then take alpha = -c0/c1 on that segment (differentiable).
-        sd, jd = s.detach(), jar.detach()
+        sd, jd, Dd = s.detach(), jar.detach(), D.detach()
         c0 = float(d.detach() @ (M @ a - q).detach()) + float((Dact * s * jar).detach().sum())
         c1 = float(d.detach() @ (M @ d).detach()) + float((Dact * s * s).detach().sum())
         seg = act.clone()
@@ -433,8 +433,8 @@ def _unrolled_newton(M, J, q, ar, D, K):
                 break
             sgn = -1.0 if bool(seg[i]) else 1.0
             seg[i] = not bool(seg[i])
-            c0 += sgn * float(D[i] * sd[i] * jd[i])
-            c1 += sgn * float(D[i] * sd[i] * sd[i])
+            c0 += sgn * float(Dd[i] * sd[i] * jd[i])
+            c1 += sgn * float(Dd[i] * sd[i] * sd[i])
         Ds = D * seg
         c0t = d @ (M @ a - q) + (Ds * s * jar).sum()
         c1t = d @ (M @ d) + (Ds * s * s).sum()
@@ -469,6 +469,79 @@ def test_unrolled_newton_derivative_matches_ift():
                 n_diff_k1 += 1
     # truncated unrolls (K = 1) carry a different derivative (Section III-E)
     assert n_diff_k1 >= 8
+
+
+def test_unrolled_oracle_matches_autograd_of_the_trace():
+    """The oracle's hand-written reverse sweep through K Newton steps equals
+    torch autograd applied to the independently written unrolled solver, for
+    every parameter, truncated (K = 1, 2, 3) and run to convergence."""
+    for w in (W.franka(10), W.tiny(10), W.quadruped(10)):
+        for b in range(w.n):
+            p = _f64(w.instance(b))
+            for K in (1, 2, 3, 50):
+                res = oracle.unrolled_one(p["M"], p["J"], p["qfrc"], p["aref"], p["D"],
+                                          p["g"], K, tol=1e-13)
+                T = {k: torch.tensor(p[k], dtype=torch.float64, requires_grad=True)
+                     for k in ("qfrc", "aref", "J", "M", "D")}
+                aK = _unrolled_newton(T["M"], T["J"], T["qfrc"], T["aref"], T["D"], K)
+                (torch.tensor(p["g"]) @ aK).backward()
+                gM = T["M"].grad.numpy()
+                assert _rel(res["a"], aK.detach().numpy()) < 1e-10
+                for key, ref in (("dqfrc", T["qfrc"].grad), ("daref", T["aref"].grad),
+                                 ("dJ", T["J"].grad), ("dD", T["D"].grad)):
+                    assert _rel(res[key].reshape(-1), ref.numpy().reshape(-1)) < 1e-9, (b, K, key)
+                assert _rel(res["dM"], 0.5 * (gM + gM.T)) < 1e-9, (b, K)
+
+
+def test_unrolled_oracle_central_differences():
+    """Central FD of a -> g^T a_K(theta) for the K-step map itself (K = 2),
+    where the sweep is stable (no mask of the trace changes within +-h)."""
+    w = W.tiny(12)
+    checked = 0
+    for b in range(w.n):
+        p = _f64(w.instance(b))
+        res = oracle.unrolled_one(p["M"], p["J"], p["qfrc"], p["aref"], p["D"], p["g"], 2)
+        for key in ("qfrc", "aref", "J", "D"):
+            grad = res["d" + key]
+            flat = grad.reshape(-1)
+            for idx in range(flat.size):
+                est = {}
+                for h in (1e-5, 1e-6):
+                    vals = []
+                    for sgn in (1.0, -1.0):
+                        q = {k2: (v.copy() if isinstance(v, np.ndarray) else v)
+                             for k2, v in p.items()}
+                        q[key].reshape(-1)[idx] += sgn * h
+                        r2 = oracle.unrolled_one(q["M"], q["J"], q["qfrc"], q["aref"],
+                                                 q["D"], q["g"], 2)
+                        vals.append(float(q["g"] @ r2["a"]))
+                    est[h] = (vals[0] - vals[1]) / (2 * h)
+                scale = max(1.0, abs(flat[idx]))
+                if abs(est[1e-5] - est[1e-6]) > 1e-6 * scale:
+                    continue              # a mask of the trace flips within h
+                checked += 1
+                assert abs(est[1e-6] - flat[idx]) <= 1e-6 * scale, (b, key, idx)
+    assert checked > 200
+
+
+def test_unrolled_derivative_approaches_ift():
+    """Run to convergence, the trace derivative equals the IFT adjoint
+    (Eq. 17) at the returned point; truncated at K = 1 it generally does not."""
+    w = W.franka(16)
+    differ = 0
+    for b in range(w.n):
+        p = _f64(w.instance(b))
+        a, act, st, it = _solve(p)
+        dq, dr, dJ, dM, dD, _, _ = oracle.adjoint_theta_one(
+            p["M"], p["J"], p["qfrc"], p["aref"], p["D"], a, p["g"])
+        res = oracle.unrolled_one(p["M"], p["J"], p["qfrc"], p["aref"], p["D"], p["g"], 100)
+        assert res["status"] == 0 and res["steps"] == it
+        assert _rel(res["a"], a) < 1e-12
+        for key, ref in (("dqfrc", dq), ("daref", dr), ("dJ", dJ), ("dM", dM), ("dD", dD)):
+            assert _rel(res[key], ref) < 1e-8, (b, key)
+        r1 = oracle.unrolled_one(p["M"], p["J"], p["qfrc"], p["aref"], p["D"], p["g"], 1)
+        differ += it > 1 and _rel(r1["dqfrc"], dq) > 1e-3
+    assert differ >= 8
 
 
 # ------------------------------------------------------------------ invariants
