@@ -287,6 +287,42 @@ void cs_plan_destroy(cs_plan* plan);
 int cs_autotune_cache_dump(char* buf, size_t len);
 int cs_autotune_cache_load(const char* text);
 
+/* ---- unrolled differentiation (the paper's comparison) ---------------- */
+
+/* The sensitivity the paper sets against the IFT adjoint (Section III-E):
+ * reverse-mode differentiation of the executed trace of at most K Newton
+ * steps.  cs_unrolled_fwd runs the solve from a0 = M^-1 qfrc (Eq. 1) for at
+ * most K = opt->max_iter steps (Eqs. 6-10; stopping early on the residual
+ * test, a non-descent direction, or an exact step that crosses no
+ * breakpoint) and records each step in `trace` and `tmask`;
+ * cs_unrolled_bwd propagates g = dL/da_K back through the recorded steps and
+ * writes dL/dqfrc, dL/daref, dL/dJ, dL/dM (symmetric M, as the *_theta entry
+ * points) and dL/dD.  Run to convergence this equals the IFT adjoint; for a
+ * truncated solve it is the derivative of the truncated map.
+ *
+ * Memory: the trace holds, per step, the factor of H_k, a_k and p_k (float
+ * pairs), alpha_k and c1_k (cs_unrolled_trace_floats(batch, K) floats: K x
+ * (total_M + 4 total_v + 2 n)) and the masks S_k, T_k
+ * (cs_unrolled_mask_bytes(batch, K) bytes: K x total_r), so it grows
+ * linearly with K, unlike cs_state.
+ *
+ * Sizes: one warp per instance only (nv_max <= 32 and m_max <= 256),
+ * CS_EUNSUPPORTED otherwise.  All pointers are device memory; `a`,
+ * `status` and `iters` are written by the forward and read by the
+ * backward (same batch, same options).  cs_unrolled_bwd uses dJ and dM as
+ * accumulators; every output must be non-NULL (daref, dJ, dD may be NULL
+ * only when m_max == 0).  Errors as for cs_solve_fwd. */
+size_t cs_unrolled_trace_floats(const cs_batch* batch, int32_t K);
+size_t cs_unrolled_mask_bytes(const cs_batch* batch, int32_t K);
+int cs_unrolled_fwd(const cs_batch* batch, const cs_options* opt, float* a,
+                    float* trace, uint8_t* tmask, int32_t* status,
+                    int32_t* iters, void* stream);
+int cs_unrolled_bwd(const cs_batch* batch, const cs_options* opt,
+                    const float* a, const float* trace, const uint8_t* tmask,
+                    int32_t* status, const int32_t* iters, const float* g,
+                    float* dqfrc, float* daref, float* dJ, float* dM,
+                    float* dD, void* stream);
+
 /* ---- serving: continuous batching ------------------------------------ */
 
 #define CS_SERVE_CONTINUOUS 0 /* admit queued requests whenever a slot frees */

@@ -67,3 +67,43 @@ def contact_solve(batch: solver.DeviceBatch, M=None, J=None, qfrc=None, aref=Non
                               batch.aref if aref is None else aref,
                               batch.D if D is None else D, tol, max_iter,
                               keep_factor)
+
+
+class UnrolledContactSolve(torch.autograd.Function):
+    """The comparison the paper makes (Section III-E): the same solve, but
+    differentiated by a reverse sweep through the recorded trace of at most K
+    Newton steps.  The saved state is the trace, whose size grows with K."""
+
+    @staticmethod
+    def forward(ctx, batch: solver.DeviceBatch, M, J, qfrc, aref, D, K=10,
+                tol=solver.DEFAULT_TOL):
+        b = batch.with_data(M=M.detach().contiguous(), J=J.detach().contiguous(),
+                            qfrc=qfrc.detach().contiguous(),
+                            aref=aref.detach().contiguous(), D=D.detach().contiguous())
+        st = solver.unrolled_fwd(b, K, tol=tol)
+        ctx.batch = b
+        ctx.state = st
+        ctx.tol = tol
+        return st.a
+
+    @staticmethod
+    def backward(ctx, grad_a):
+        b = ctx.batch
+        dq, dr, dJ, dM, dD = solver.unrolled_bwd(b, ctx.state, grad_a.contiguous(),
+                                                 tol=ctx.tol)
+        ng = ctx.needs_input_grad
+        shape = lambda x, ref: (x[:ref.numel()].view_as(ref) if ref.numel()
+                                else torch.zeros_like(ref))
+        return (None, shape(dM, b.M) if ng[1] else None, shape(dJ, b.J) if ng[2] else None,
+                shape(dq, b.qfrc) if ng[3] else None, shape(dr, b.aref) if ng[4] else None,
+                shape(dD, b.D) if ng[5] else None, None, None)
+
+
+def contact_solve_unrolled(batch: solver.DeviceBatch, M=None, J=None, qfrc=None,
+                           aref=None, D=None, K=10, tol=solver.DEFAULT_TOL):
+    """a after at most K Newton steps, differentiated through its trace."""
+    return UnrolledContactSolve.apply(batch, batch.M if M is None else M,
+                                      batch.J if J is None else J,
+                                      batch.qfrc if qfrc is None else qfrc,
+                                      batch.aref if aref is None else aref,
+                                      batch.D if D is None else D, K, tol)

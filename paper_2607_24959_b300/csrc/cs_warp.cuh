@@ -158,6 +158,7 @@ struct WarpSolver {
   float ah, al;          // a = ah + al
   float qf, gj;          // qfrc_j, g_j
   float r, maq;          // r_j, (M a - qfrc)_j
+  float rlo;             // low part of the compensated r (r + rlo)
   float fmax;            // max |f| at the current point
   float qmax;            // max |qfrc|
 
@@ -569,9 +570,12 @@ struct WarpSolver {
     const float lo1 = __fadd_rn(e1, mc);
     maq = __fadd_rn(t1, lo1);
     two_sum(t1, js, t2, e2);
-    r = __fadd_rn(t2, __fadd_rn(lo1, __fadd_rn(e2, jc)));
+    const float lo2 = __fadd_rn(lo1, __fadd_rn(e2, jc));
+    r = __fadd_rn(t2, lo2);
+    rlo = __fsub_rn(lo2, __fsub_rn(r, t2));
     if (lane >= NV) {
       r = 0.f;
+      rlo = 0.f;
       maq = 0.f;
     }
     const float rm = warp_max(fabsf(r));
@@ -752,8 +756,14 @@ struct WarpSolver {
   // Solve H w = g at the current point (Eq. 17) by iterative refinement with
   // compensated residuals.  Leaves w in (wh, wl), lambda = D_act . J w in
   // Lam() for every row < m.
-  __device__ __forceinline__ void adjoint(float& wh, float& wl) {
-    wh = chol_solve(gj);
+  __device__ __forceinline__ void adjoint(float& wh, float& wl) { solve_refined(gj, 0.f, wh, wl); }
+
+  // H w = rhs + rhs_lo (spread per lane) with H = M + sum over the active
+  // list of D_i J_i^T J_i factored in Ls(): FP32 factor as preconditioner,
+  // residuals rhs - M w - J^T (D_act . J w) accumulated with error-free
+  // transformations.
+  __device__ __forceinline__ void solve_refined(float rhs, float rhs_lo, float& wh, float& wl) {
+    wh = chol_solve(rhs);
     wl = 0.f;
     float* Lm = Lam();
     float* Lml = Lamlo();
@@ -801,9 +811,9 @@ struct WarpSolver {
       jt_active(Lm, Lml, js, jc);
       m_times(vh, vl, ms, mc);
       float t1, e1, t2, e2;
-      two_sum(gj, -ms, t1, e1);
+      two_sum(rhs, -ms, t1, e1);
       two_sum(t1, -js, t2, e2);
-      float rho = __fadd_rn(t2, __fsub_rn(__fadd_rn(e1, e2), __fadd_rn(mc, jc)));
+      float rho = __fadd_rn(t2, __fsub_rn(__fadd_rn(__fadd_rn(e1, e2), rhs_lo), __fadd_rn(mc, jc)));
       if (lane >= NV) rho = 0.f;
       const float dw = chol_solve(rho);
       dmax_prev = warp_max(fabsf(dw));

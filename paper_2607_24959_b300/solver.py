@@ -181,6 +181,65 @@ def solve_adjoint(batch: DeviceBatch, a, state: State, g, tol=DEFAULT_TOL,
     return dq, dr, dJ
 
 
+@dataclasses.dataclass
+class UnrolledState:
+    """What the unrolled reverse sweep needs: the trace of the executed K
+    steps (grows linearly with K), the returned a, status and step counts."""
+
+    a: torch.Tensor
+    trace: torch.Tensor
+    tmask: torch.Tensor
+    status: torch.Tensor
+    iters: torch.Tensor
+    K: int
+
+    def nbytes(self) -> int:
+        """Bytes kept between the forward and the reverse sweep (a excluded,
+        as for State)."""
+        return sum(t.numel() * t.element_size()
+                   for t in (self.trace, self.tmask, self.status, self.iters))
+
+
+def unrolled_fwd(batch: DeviceBatch, K: int, tol=DEFAULT_TOL) -> UnrolledState:
+    """At most K Newton steps with their trace recorded (cs_unrolled_fwd)."""
+    lib = _lib.load()
+    dev = batch.M.device
+    b = batch.cstruct()
+    nf = int(lib.cs_unrolled_trace_floats(ctypes.byref(b), int(K)))
+    nm = int(lib.cs_unrolled_mask_bytes(ctypes.byref(b), int(K)))
+    st = UnrolledState(
+        a=torch.empty(max(batch.total_v, 1), dtype=torch.float32, device=dev),
+        trace=torch.empty(max(nf, 1), dtype=torch.float32, device=dev),
+        tmask=torch.empty(max(nm, 1), dtype=torch.uint8, device=dev),
+        status=torch.empty(max(batch.n, 1), dtype=torch.int32, device=dev),
+        iters=torch.empty(max(batch.n, 1), dtype=torch.int32, device=dev), K=int(K))
+    o = options(tol, K, False, 0)
+    _lib.check(lib.cs_unrolled_fwd(ctypes.byref(b), ctypes.byref(o), _ptr(st.a),
+                                   _ptr(st.trace), _ptr(st.tmask), _ptr(st.status),
+                                   _ptr(st.iters), _stream()), "cs_unrolled_fwd")
+    return st
+
+
+def unrolled_bwd(batch: DeviceBatch, st: UnrolledState, g, tol=DEFAULT_TOL):
+    """Reverse sweep through the recorded steps (cs_unrolled_bwd); returns
+    (dqfrc, daref, dJ, dM, dD) packed like qfrc, aref, J, M and D."""
+    lib = _lib.load()
+    dev = batch.M.device
+    dq = torch.empty(max(batch.total_v, 1), dtype=torch.float32, device=dev)
+    dr = torch.empty(max(batch.total_r, 1), dtype=torch.float32, device=dev)
+    dJ = torch.empty(max(batch.J.numel(), 1), dtype=torch.float32, device=dev)
+    dM = torch.empty(max(batch.M.numel(), 1), dtype=torch.float32, device=dev)
+    dD = torch.empty(max(batch.total_r, 1), dtype=torch.float32, device=dev)
+    b = batch.cstruct()
+    o = options(tol, st.K, False, 0)
+    g = g.contiguous()
+    _lib.check(lib.cs_unrolled_bwd(ctypes.byref(b), ctypes.byref(o), _ptr(st.a),
+                                   _ptr(st.trace), _ptr(st.tmask), _ptr(st.status),
+                                   _ptr(st.iters), _ptr(g), _ptr(dq), _ptr(dr), _ptr(dJ),
+                                   _ptr(dM), _ptr(dD), _stream()), "cs_unrolled_bwd")
+    return dq, dr, dJ, dM, dD
+
+
 def fused_workspace_bytes(n: int) -> int:
     return int(_lib.load().cs_fused_workspace_bytes(int(n)))
 

@@ -1,0 +1,155 @@
+"""Unrolled reverse-mode differentiation (the comparison of Section III-E):
+the CUDA trace-recording forward and reverse sweep against the FP64 oracle's
+unrolled derivative on the same seeded inputs, its limit (equal to the IFT
+adjoint of Eq. 17 once converged), and the memory contrast: the trace grows
+linearly with the step cap K while the IFT state does not."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_24959_b300 import autograd as csag, solver, workloads as W
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("dqfrc", "daref", "dJ", "dM", "dD")
+
+
+def _gpu_unrolled(batch, w, K):
+    st = solver.unrolled_fwd(batch, K)
+    g = torch.from_numpy(np.ascontiguousarray(w.g, np.float32)).to(batch.M.device)
+    grads = solver.unrolled_bwd(batch, st, g)
+    torch.cuda.synchronize()
+    out = dict(a=st.a.cpu().numpy(), status=st.status.cpu().numpy(),
+               iters=st.iters.cpu().numpy())
+    for k, v in zip(KEYS, grads):
+        out[k] = v.cpu().numpy()
+    return out
+
+
+def _segments(w, b):
+    e = w.inst[b]
+    nv, m = int(e["nv"]), int(e["m"])
+    ov, orr, oJ, oM = (int(e[k]) for k in ("off_v", "off_r", "off_J", "off_M"))
+    return dict(a=slice(ov, ov + nv), dqfrc=slice(ov, ov + nv), daref=slice(orr, orr + m),
+                dD=slice(orr, orr + m), dJ=slice(oJ, oJ + m * nv), dM=slice(oM, oM + nv * nv))
+
+
+def _trace_tie(w, b, K):
+    """Smallest relative distance of a row from its mask decision along the
+    FP64 trace: |jar_i| for S_k and |jar_i + alpha_k s_i| for T_k, each over
+    sum_j |J_ij a_j| + |aref_i| (the scale at which FP32 rounds them)."""
+    p = {k: np.asarray(v, np.float64) for k, v in w.instance(b).items()}
+    M, J, q, ar, D = p["M"], p["J"], p["qfrc"], p["aref"], p["D"]
+    a = np.linalg.solve(M, q)
+    tie = np.inf
+    for _ in range(K):
+        if J.shape[0] == 0:
+            break
+        jar = J @ a - ar
+        S = jar < 0
+        r = M @ a - q + J.T @ (D * np.where(S, jar, 0.0))
+        scale = np.abs(J) @ np.abs(a) + np.abs(ar)
+        tie = min(tie, float(np.min(np.abs(jar) / scale)))
+        H = M + J[S].T @ (D[S, None] * J[S])
+        pp = -np.linalg.solve(H, r)
+        if np.array_equal((J @ (a + pp) - ar) < 0, S):
+            break
+        al = oracle.line_search_one(M, J, q, ar, D, a, pp)
+        a = a + al * pp
+        tie = min(tie, float(np.min(np.abs(J @ a - ar) / (np.abs(J) @ np.abs(a) + np.abs(ar)))))
+    return tie
+
+
+def _compare(w, gpu, ref, what, K, max_bad_frac=0.01):
+    """Per instance: same number of executed steps, a_K within 1e-4 and every
+    gradient within 1e-3 (relative to the oracle's infinity norm).  A trace
+    whose S or T mask is decided at a near-tie (a row within 1e-4 of its
+    boundary, relative to its scale) may be decided differently in FP32 and
+    FP64 and then differentiates another map: only such instances may fail,
+    and at most 1 % of them."""
+    worst = {k: 0.0 for k in ("a",) + KEYS}
+    bad, steps_differ = [], 0
+    n = w.n
+    for b in range(n):
+        if ref["status"][b] not in (0, 1):
+            continue
+        if gpu["iters"][b] != ref["iters"][b]:
+            steps_differ += 1
+            bad.append((b, "steps", int(gpu["iters"][b]), int(ref["iters"][b])))
+            continue
+        seg = _segments(w, b)
+        errs = {k: parity.rel(gpu[k][seg[k]], ref[k][seg[k]]) for k in ("a",) + KEYS}
+        for k, v in errs.items():
+            worst[k] = max(worst[k], v)
+        if errs["a"] > parity.A_TOL or any(errs[k] > parity.G_TOL for k in KEYS):
+            bad.append((b, errs))
+    ties = {b[0]: _trace_tie(w, b[0], K) for b in bad}
+    msg = (f"{what}: worst {worst}, steps differ {steps_differ}, bad {len(bad)} "
+           f"(trace ties {ties}) e.g. {bad[:3]}")
+    print(msg)
+    assert len(bad) <= max_bad_frac * n, msg
+    assert all(t < 1e-4 for t in ties.values()), msg
+    return worst
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 10])
+def test_unrolled_matches_oracle_franka(cuda_device, K):
+    w = W.franka(n=512, seed=61)                   # nv 9, m 64, cond(M) 1e3
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    gpu = _gpu_unrolled(batch, w, K)
+    ref = oracle.unrolled_workload(w, K, threads=8)
+    _compare(w, gpu, ref, f"franka K={K}", K)
+
+
+@pytest.mark.parametrize("K", [1, 4])
+def test_unrolled_matches_oracle_ragged(cuda_device, K):
+    for w in (W.quadruped(n=512, seed=62), W.tiny(n=512, seed=63)):
+        batch = solver.DeviceBatch.from_workload(w, cuda_device)
+        gpu = _gpu_unrolled(batch, w, K)
+        ref = oracle.unrolled_workload(w, K, threads=8)
+        _compare(w, gpu, ref, f"{w.name} K={K}", K)
+
+
+def test_unrolled_converged_equals_ift(cuda_device):
+    w = W.quadruped(n=1024, seed=64)
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    unr = _gpu_unrolled(batch, w, 50)
+    ift = parity.run_gpu_fused(batch, w, theta=True)
+    assert np.all(unr["status"][:w.n] == 0)
+    worst = {k: 0.0 for k in ("a",) + KEYS}
+    for b in range(w.n):
+        seg = _segments(w, b)
+        for k in worst:
+            worst[k] = max(worst[k], parity.rel(unr[k][seg[k]], ift[k][seg[k]]))
+    print("unrolled(K=50) vs IFT:", worst)
+    assert worst["a"] <= parity.A_TOL and all(worst[k] <= parity.G_TOL for k in KEYS), worst
+
+
+def test_unrolled_autograd_and_memory_growth(cuda_device):
+    """The autograd wrapper returns the oracle's unrolled gradients, and the
+    state kept for the backward grows linearly with K (the trace) while the
+    IFT state is the same for every K."""
+    w = W.generate("mem", 1024, 24, 4, seed=65, cond=1e2)   # nv 24, 4 contacts
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    g = torch.from_numpy(w.g).to(cuda_device)
+    J = batch.J.clone().requires_grad_(True)
+    M = batch.M.clone().requires_grad_(True)
+    a = csag.contact_solve_unrolled(batch, J=J, M=M, K=3)
+    (a[:g.numel()] * g).sum().backward()
+    torch.cuda.synchronize()
+    ref = oracle.unrolled_workload(w, 3, threads=8)
+    seg_ok = 0
+    for b in range(w.n):
+        s = _segments(w, b)
+        if (parity.rel(J.grad.cpu().numpy()[s["dJ"]], ref["dJ"][s["dJ"]]) <= parity.G_TOL and
+                parity.rel(M.grad.cpu().numpy()[s["dM"]], ref["dM"][s["dM"]]) <= parity.G_TOL):
+            seg_ok += 1
+    assert seg_ok >= 0.99 * w.n
+    unrolled = [solver.unrolled_fwd(batch, K).nbytes() for K in range(1, 11)]
+    ift = [solver.alloc_state(batch, True).nbytes() for _ in range(1, 11)]
+    steps = np.diff(unrolled)
+    assert np.all(steps == steps[0]) and steps[0] > 0
+    assert len(set(ift)) == 1
+    print("state bytes K=1..10: unrolled", unrolled, "IFT", ift[0])
