@@ -13,6 +13,7 @@ on a bounded sample instead (the reference arm of this benchmark).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -400,11 +401,114 @@ def run_gpu(args):
         del plan, out, batch
         torch.cuda.empty_cache()
         line["serve"] = run_serve(args)
+    if not args.no_memory and world == 1:
+        line["adjoint_memory"] = run_memory(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, max_instances=args.cpu_sample)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_memory(args):
+    """The paper's memory comparison (Section III-E, Fig. 3), on B300 with
+    this library's kernels: device bytes for differentiating the solve with
+    the IFT adjoint (state independent of K) against unrolled reverse mode
+    (trace grows with K), through the autograd wrappers, B = 1024 instances.
+    Three sweeps as in the figure's panels, where the sizes fit the
+    one-warp-per-instance kernels of the unrolled path (nv <= 32, m <= 256):
+    step cap K = 1..10 at nv 24 with 4 contacts; contacts 1..64 at nv 6,
+    K = 5; N particles (nv 6N, N contacts) for N = 1..5, K = 5."""
+    import torch
+    from paper_2607_24959_b300 import autograd as csag, solver, workloads as W
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+
+    def measure(w, K):
+        batch = solver.DeviceBatch.from_workload(w, dev)
+        g = torch.from_numpy(w.g).to(dev)
+        res = {}
+        for name in ("ift", "unrolled"):
+            def once():
+                J = batch.J.clone().requires_grad_(True)
+                q = batch.qfrc.clone().requires_grad_(True)
+                if name == "ift":
+                    a = csag.contact_solve(batch, J=J, qfrc=q, max_iter=K)
+                else:
+                    a = csag.contact_solve_unrolled(batch, J=J, qfrc=q, K=K)
+                (a[:g.numel()] * g).sum().backward()
+                return J, q
+            once()
+            times = []
+            for rep in range(3):
+                # autograd graphs of earlier calls are freed before the peak
+                # is taken, and the collector does not run inside it
+                torch.cuda.synchronize()
+                gc.collect()
+                gc.disable()
+                try:
+                    torch.cuda.reset_peak_memory_stats(dev)
+                    base = torch.cuda.memory_allocated(dev)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    J, q = once()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    peak = torch.cuda.max_memory_allocated(dev) - base
+                finally:
+                    gc.enable()
+                times.append(e0.elapsed_time(e1))
+                del J, q
+            if name == "ift":
+                kept = solver.alloc_state(batch, True).nbytes()
+            else:
+                kept = solver.unrolled_fwd(batch, K).nbytes()
+            res[name] = {"kept_bytes": int(kept), "peak_bytes": int(peak),
+                         "ms": round(float(np.median(times)), 4)}
+        del batch, g
+        torch.cuda.empty_cache()
+        return res
+
+    out = {"method": "bytes kept between forward and backward (IFT: a_lo, active set, "
+                     "factor of H(a*); unrolled: per-step factor, a_k, p_k, alpha_k, c1_k, "
+                     "masks) and peak device bytes allocated during one forward + backward "
+                     "through the autograd wrappers (torch allocator, inputs excluded), FP32; "
+                     "J and qfrc require grad",
+           "batch": 1024}
+    ks = list(range(1, 11))
+    w = W.generate("mem-iter", 1024, 24, 4, seed=71, cond=1e2)
+    rows = [measure(w, K) for K in ks]
+    out["iterations"] = {
+        "config": "nv 24, 4 contacts (16 rows), cond(M) 1e2, B 1024", "K": ks,
+        "ift_peak": [r["ift"]["peak_bytes"] for r in rows],
+        "unrolled_peak": [r["unrolled"]["peak_bytes"] for r in rows],
+        "ift_kept": [r["ift"]["kept_bytes"] for r in rows],
+        "unrolled_kept": [r["unrolled"]["kept_bytes"] for r in rows],
+        "ift_ms": [r["ift"]["ms"] for r in rows],
+        "unrolled_ms": [r["unrolled"]["ms"] for r in rows]}
+    it = out["iterations"]
+    it["ift_peak_change_K1_to_K10"] = it["ift_peak"][-1] / it["ift_peak"][0] - 1.0
+    it["unrolled_peak_growth_K1_to_K10"] = it["unrolled_peak"][-1] / it["unrolled_peak"][0]
+    ncs = [1, 2, 4, 8, 16, 32, 64]
+    rows = [measure(W.generate(f"mem-c{nc}", 1024, 6, nc, seed=72 + nc, cond=1e2), 5)
+            for nc in ncs]
+    out["contacts"] = {
+        "config": "nv 6, K 5, B 1024", "contacts": ncs,
+        "ift_peak": [r["ift"]["peak_bytes"] for r in rows],
+        "unrolled_peak": [r["unrolled"]["peak_bytes"] for r in rows],
+        "unrolled_over_ift": [r["unrolled"]["peak_bytes"] / r["ift"]["peak_bytes"]
+                              for r in rows]}
+    Ns = [1, 2, 3, 4, 5]
+    rows = [measure(W.generate(f"mem-n{N}", 1024, 6 * N, N, seed=80 + N, cond=1e2), 5)
+            for N in Ns]
+    out["dof"] = {
+        "config": "N particles: nv 6N, N contacts, K 5, B 1024", "N": Ns,
+        "ift_peak": [r["ift"]["peak_bytes"] for r in rows],
+        "unrolled_peak": [r["unrolled"]["peak_bytes"] for r in rows],
+        "unrolled_over_ift": [r["unrolled"]["peak_bytes"] / r["ift"]["peak_bytes"]
+                              for r in rows]}
+    return out
 
 
 def run_e2e(args, w, batch, dev, kw, world):
@@ -452,6 +556,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=32768)
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-memory", action="store_true",
+                    help="skip the IFT vs unrolled differentiation memory sweeps")
     ap.add_argument("--e2e-chunks", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-rate", type=float, default=50000.0)

@@ -82,15 +82,22 @@ class UnrolledContactSolve(torch.autograd.Function):
                             aref=aref.detach().contiguous(), D=D.detach().contiguous())
         st = solver.unrolled_fwd(b, K, tol=tol)
         ctx.batch = b
-        ctx.state = st
+        # the output goes through save_for_backward (an attribute holding it
+        # would form a reference cycle with the graph)
+        ctx.save_for_backward(st.a)
+        ctx.trace = (st.trace, st.tmask, st.status, st.iters, st.K)
         ctx.tol = tol
+        ctx.mark_non_differentiable()
         return st.a
 
     @staticmethod
     def backward(ctx, grad_a):
         b = ctx.batch
-        dq, dr, dJ, dM, dD = solver.unrolled_bwd(b, ctx.state, grad_a.contiguous(),
-                                                 tol=ctx.tol)
+        (a,) = ctx.saved_tensors
+        trace, tmask, status, iters, K = ctx.trace
+        st = solver.UnrolledState(a=a, trace=trace, tmask=tmask, status=status, iters=iters,
+                                  K=K)
+        dq, dr, dJ, dM, dD = solver.unrolled_bwd(b, st, grad_a.contiguous(), tol=ctx.tol)
         ng = ctx.needs_input_grad
         shape = lambda x, ref: (x[:ref.numel()].view_as(ref) if ref.numel()
                                 else torch.zeros_like(ref))
