@@ -12,6 +12,9 @@ ctypes.  Every function follows the paper's Section III:
                    an exact line search and exact termination.
 * ``adjoint_one``  the transposed solve of Eq. 17 at the returned point.
 * ``adjoint_theta_one`` the same, adding the M and D terms of Eq. 17.
+* ``ell_*``       the same solve and adjoint with MuJoCo's round Coulomb
+                   cone (three rows per contact, Eqs. 2-5) instead of the
+                   pyramid rows.
 * ``unrolled_one`` / ``unrolled_workload``  the derivative through the
                    executed trace of at most K Newton steps (the unrolled
                    reverse-mode sensitivity the paper compares with IFT).
@@ -90,6 +93,19 @@ def _load():
             lib.oracle_unrolled.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp, ci,
                                             cd, dp, ip, dp, dp, dp, dp, dp]
             lib.oracle_unrolled.restype = ci
+            lib.oracle_ell_cone.argtypes = [dp, cd, cd, cd, dp, dp, dp]
+            lib.oracle_ell_cone.restype = ci
+            lib.oracle_ell_solve.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp, cd, ci,
+                                             dp, u8p, ip]
+            lib.oracle_ell_solve.restype = ci
+            lib.oracle_ell_adjoint.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp, dp, dp,
+                                               dp, dp, dp, dp, dp, dp, u8p]
+            lib.oracle_ell_adjoint.restype = ci
+            lib.oracle_ell_objective.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp, dp]
+            lib.oracle_ell_objective.restype = cd
+            lib.oracle_ell_line_search.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp, dp,
+                                                   dp]
+            lib.oracle_ell_line_search.restype = cd
             lib.oracle_line_search.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp,
                                                dp]
             lib.oracle_line_search.restype = cd
@@ -215,6 +231,128 @@ def unrolled_workload(w, K, idx=None, tol=DEFAULT_TOL, threads=1):
             out["dM"][oM:oM + nv * nv] = res["dM"].ravel()
             out["status"][int(b)] = res["status"]
             out["iters"][int(b)] = res["steps"]
+
+    if threads <= 1 or todo.size < 2:
+        run(todo)
+    else:
+        ts = [threading.Thread(target=run, args=(part,))
+              for part in np.array_split(todo, threads) if part.size]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+    return out
+
+
+# ---- round (elliptic) cone: three rows per contact (normal, two tangents),
+# D_N = D[3c], D_T = D[3c+1] (D[3c+2] not read), mu = mu[3c].
+
+def _c(x):
+    return x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def ell_cone_one(u, DN, DT, mu):
+    """(zone, s, grad[3], hess[3x3]) of one contact's round-cone cost."""
+    lib = _load()
+    uu = _d(u)[0]
+    s = ctypes.c_double(0.0)
+    g = np.zeros(3)
+    h = np.zeros(9)
+    z = lib.oracle_ell_cone(_c(uu), float(DN), float(DT), float(mu), ctypes.byref(s),
+                            _c(g), _c(h))
+    return int(z), float(s.value), g, h.reshape(3, 3)
+
+
+def ell_solve_one(M, J, qfrc, aref, D, mu, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER):
+    """Returns (a, zone per row, status, iters) with the round cone."""
+    lib = _load()
+    nv, m, arrs = _prob(M, J, qfrc, aref, D)
+    muu = _d(mu)[0]
+    a = np.zeros(nv)
+    zone = np.zeros(max(m, 1), np.uint8)
+    it = ctypes.c_int(0)
+    st = lib.oracle_ell_solve(nv, m, *[p for _, p in arrs], _c(muu), float(tol),
+                              int(max_iter), _c(a),
+                              zone.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                              ctypes.byref(it))
+    return a, zone[:m].copy(), int(st), int(it.value)
+
+
+def ell_adjoint_one(M, J, qfrc, aref, D, mu, a, g):
+    """Eq. 17 with the round cone at a: dict of dqfrc, daref, dJ, dM, dD, dmu,
+    zone, status."""
+    lib = _load()
+    nv, m, arrs = _prob(M, J, qfrc, aref, D)
+    muu, aa, gg = _d(mu)[0], _d(a)[0], _d(g)[0]
+    out = dict(dqfrc=np.zeros(nv), daref=np.zeros(max(m, 1)), dJ=np.zeros(max(m * nv, 1)),
+               dM=np.zeros(nv * nv), dD=np.zeros(max(m, 1)), dmu=np.zeros(max(m, 1)))
+    zone = np.zeros(max(m, 1), np.uint8)
+    st = lib.oracle_ell_adjoint(nv, m, *[p for _, p in arrs], _c(muu), _c(aa), _c(gg),
+                                *[_c(out[k]) for k in ("dqfrc", "daref", "dJ", "dM", "dD",
+                                                       "dmu")],
+                                zone.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    out["daref"] = out["daref"][:m]
+    out["dD"] = out["dD"][:m]
+    out["dmu"] = out["dmu"][:m]
+    out["dJ"] = out["dJ"][:m * nv].reshape(m, nv)
+    out["dM"] = out["dM"].reshape(nv, nv)
+    out["zone"] = zone[:m].copy()
+    out["status"] = int(st)
+    return out
+
+
+def ell_objective_one(M, J, qfrc, aref, D, mu, a):
+    lib = _load()
+    nv, m, arrs = _prob(M, J, qfrc, aref, D)
+    return float(lib.oracle_ell_objective(nv, m, *[p for _, p in arrs], _c(_d(mu)[0]),
+                                          _c(_d(a)[0])))
+
+
+def ell_line_search_one(M, J, qfrc, aref, D, mu, a, p):
+    lib = _load()
+    nv, m, arrs = _prob(M, J, qfrc, aref, D)
+    return float(lib.oracle_ell_line_search(nv, m, *[q for _, q in arrs], _c(_d(mu)[0]),
+                                            _c(_d(a)[0]), _c(_d(p)[0])))
+
+
+def ell_solve_workload(w, idx=None, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
+                       threads=1):
+    """Round-cone forward + adjoint (with the workload's g and mu) over a
+    packed batch: packed a, dqfrc, daref, dJ, dM, dD, dmu, zone and
+    per-instance status and iters; instances outside ``idx`` stay zero."""
+    inst = w.inst
+    n = inst.shape[0]
+    out = dict(a=np.zeros(w.qfrc.size), dqfrc=np.zeros(w.qfrc.size),
+               daref=np.zeros(w.aref.size), dJ=np.zeros(w.J.size), dM=np.zeros(w.M.size),
+               dD=np.zeros(w.aref.size), dmu=np.zeros(w.aref.size),
+               zone=np.zeros(w.aref.size, np.uint8), status=np.full(n, -1, np.int32),
+               iters=np.zeros(n, np.int32))
+    todo = np.arange(n) if idx is None else np.asarray(idx).ravel()
+
+    def run(bs):
+        for b in bs:
+            e = inst[int(b)]
+            nv, m = int(e["nv"]), int(e["m"])
+            ov, orr, oJ, oM = (int(e[k]) for k in ("off_v", "off_r", "off_J", "off_M"))
+            p = w.instance(int(b))
+            a, zone, st, it = ell_solve_one(p["M"], p["J"], p["qfrc"], p["aref"], p["D"],
+                                            p["mu"], tol, max_iter)
+            out["a"][ov:ov + nv] = a
+            out["status"][int(b)] = st
+            out["iters"][int(b)] = it
+            out["zone"][orr:orr + m] = zone
+            if st in (2, 3, 4):
+                continue
+            adj = ell_adjoint_one(p["M"], p["J"], p["qfrc"], p["aref"], p["D"], p["mu"], a,
+                                  p["g"])
+            if adj["status"]:
+                out["status"][int(b)] = adj["status"]
+            out["dqfrc"][ov:ov + nv] = adj["dqfrc"]
+            out["daref"][orr:orr + m] = adj["daref"]
+            out["dD"][orr:orr + m] = adj["dD"]
+            out["dmu"][orr:orr + m] = adj["dmu"]
+            out["dJ"][oJ:oJ + m * nv] = adj["dJ"].ravel()
+            out["dM"][oM:oM + nv * nv] = adj["dM"].ravel()
 
     if threads <= 1 or todo.size < 2:
         run(todo)

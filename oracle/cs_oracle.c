@@ -387,6 +387,337 @@ void oracle_batch(int lo, int hi, const int32_t *nv, const int32_t *m,
   }
 }
 
+/* ---- round (elliptic) Coulomb cone (Eqs. 2-5 as the paper states them) -- */
+
+/* One contact c owns three rows: 3c (normal) and 3c+1, 3c+2 (tangents), with
+ * u = J a - aref on those rows, D_N = D[3c], D_T = D[3c+1] (one tangential
+ * regularisation for both tangent rows; D[3c+2] is not read) and
+ * mu = mu[3c].  Its cost is the weighted distance of Eq. 5,
+ *   s(u) = min over z in K* of 1/2 (u - z)^T diag(D_N, D_T, D_T) (u - z),
+ *   K* = {z : z_N >= mu |z_T|}  (dual of the cone of Eq. 2, Eq. 3).
+ * With x = diag(D)^(1/2) u the weighted distance is the Euclidean distance of
+ * x to the second-order cone {x_N >= mu~ |x_T|}, mu~ = mu sqrt(D_N / D_T),
+ * whose projection has three regions (t = |u_T|):
+ *   zone 0 (u inside K*):          u_N >= mu t                      s = 0
+ *   zone 2 (x in the polar cone):  mu D_N u_N + D_T t <= 0          s = 1/2 (D_N u_N^2 + D_T t^2)
+ *   zone 1 (between):              phi = mu t - u_N > 0,            s = 1/2 Dm phi^2,
+ *                                  Dm = D_N / (1 + mu^2 D_N / D_T).
+ * Writes s, the gradient (3) and the Hessian (3x3 row-major) and returns the
+ * zone.  In zone 1, grad = Dm phi (-1, mu uhat) with uhat = u_T / t and
+ * hess = Dm [(-1, mu uhat)(-1, mu uhat)^T + phi mu / t (0 (+) (I - uhat uhat^T))]. */
+static int ell_cone(const double *u, double DN, double DT, double mu, double *s,
+                    double *grad, double *hess) {
+  const double uN = u[0], u1 = u[1], u2 = u[2];
+  const double t = sqrt(u1 * u1 + u2 * u2);
+  for (int k = 0; k < 9; ++k) hess[k] = 0.0;
+  if (uN >= mu * t) {
+    *s = 0.0;
+    grad[0] = grad[1] = grad[2] = 0.0;
+    return 0;
+  }
+  if (mu * DN * uN + DT * t <= 0.0) {
+    *s = 0.5 * (DN * uN * uN + DT * t * t);
+    grad[0] = DN * uN;
+    grad[1] = DT * u1;
+    grad[2] = DT * u2;
+    hess[0] = DN;
+    hess[4] = DT;
+    hess[8] = DT;
+    return 2;
+  }
+  const double Dm = DN / (1.0 + mu * mu * DN / DT);
+  const double phi = mu * t - uN;
+  const double h1 = t > 0.0 ? u1 / t : 0.0, h2 = t > 0.0 ? u2 / t : 0.0;
+  const double gv[3] = {-1.0, mu * h1, mu * h2};
+  *s = 0.5 * Dm * phi * phi;
+  for (int k = 0; k < 3; ++k) grad[k] = Dm * phi * gv[k];
+  for (int j = 0; j < 3; ++j)
+    for (int k = 0; k < 3; ++k) hess[3 * j + k] = Dm * gv[j] * gv[k];
+  if (t > 0.0) {
+    const double c = Dm * phi * mu / t;
+    hess[4] += c * (1.0 - h1 * h1);
+    hess[5] += c * (-h1 * h2);
+    hess[7] += c * (-h2 * h1);
+    hess[8] += c * (1.0 - h2 * h2);
+  }
+  return 1;
+}
+
+/* The cone pieces on their own, for pinning them: s, gradient, Hessian. */
+int oracle_ell_cone(const double *u, double DN, double DT, double mu, double *s,
+                    double *grad, double *hess) {
+  return ell_cone(u, DN, DT, mu, s, grad, hess);
+}
+
+/* u = J a - aref, per-contact zone / gradient / Hessian block, Ma, J^T grad,
+ * r = Ma - qfrc + J^T grad (Eq. 6 with s of the round cone).  Returns the
+ * stopping scale max(1, |qfrc|, |Ma|, |J^T grad|); *cost += sum_c s_c. */
+static double ell_residual(const problem *P, const double *mu, const double *a,
+                           double *u, uint8_t *zone, double *grad,
+                           double *hessb, double *Ma, double *Jtf, double *r,
+                           double *cost) {
+  const int nv = P->nv, m = P->m, nc = m / 3;
+  for (int i = 0; i < m; ++i) {
+    double v = 0.0;
+    for (int k = 0; k < nv; ++k) v += P->J[i * nv + k] * a[k];
+    u[i] = v - P->aref[i];
+  }
+  double sc = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    double s;
+    const int z = ell_cone(u + 3 * c, P->D[3 * c], P->D[3 * c + 1], mu[3 * c], &s,
+                           grad + 3 * c, hessb + 9 * c);
+    zone[3 * c] = zone[3 * c + 1] = zone[3 * c + 2] = (uint8_t)z;
+    sc += s;
+  }
+  if (cost) *cost += sc;
+  for (int j = 0; j < nv; ++j) {
+    double v = 0.0, t = 0.0;
+    for (int k = 0; k < nv; ++k) v += P->M[j * nv + k] * a[k];
+    for (int i = 0; i < 3 * nc; ++i) t += P->J[i * nv + j] * grad[i];
+    Ma[j] = v;
+    Jtf[j] = t;
+    r[j] = v - P->qfrc[j] + t;
+  }
+  double scale = 1.0, v;
+  if ((v = inf_norm(nv, P->qfrc)) > scale) scale = v;
+  if ((v = inf_norm(nv, Ma)) > scale) scale = v;
+  if ((v = inf_norm(nv, Jtf)) > scale) scale = v;
+  return scale;
+}
+
+/* H = M + sum_c J_c^T hess_c J_c (Eq. 9 with the block Hessians). */
+static void ell_newton_matrix(const problem *P, const double *hessb, double *H) {
+  const int nv = P->nv, nc = P->m / 3;
+  memcpy(H, P->M, sizeof(double) * nv * nv);
+  for (int c = 0; c < nc; ++c) {
+    const double *Jc = P->J + (size_t)3 * c * nv, *Hc = hessb + 9 * c;
+    for (int j = 0; j < nv; ++j)
+      for (int k = 0; k < nv; ++k) {
+        double v = 0.0;
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) v += Jc[p * nv + j] * Hc[3 * p + q] * Jc[q * nv + k];
+        H[j * nv + k] += v;
+      }
+  }
+}
+
+/* phi'(alpha) for phi(alpha) = L(a + alpha p): p^T (M (a + alpha p) - qfrc)
+ * + sum_c grad_c(u_c + alpha v_c) . v_c, with v = J p. */
+static double ell_dphi(const problem *P, const double *mu, const double *a,
+                       const double *p, double alpha) {
+  const int nv = P->nv, nc = P->m / 3;
+  double d = 0.0;
+  for (int j = 0; j < nv; ++j) {
+    double v = 0.0;
+    for (int k = 0; k < nv; ++k) v += P->M[j * nv + k] * (a[k] + alpha * p[k]);
+    d += p[j] * (v - P->qfrc[j]);
+  }
+  for (int c = 0; c < nc; ++c) {
+    double uc[3], vc[3], s, g[3], h[9];
+    for (int q = 0; q < 3; ++q) {
+      const double *Ji = P->J + (size_t)(3 * c + q) * nv;
+      double x = 0.0, y = 0.0;
+      for (int k = 0; k < nv; ++k) {
+        x += Ji[k] * a[k];
+        y += Ji[k] * p[k];
+      }
+      uc[q] = x - P->aref[3 * c + q] + alpha * y;
+      vc[q] = y;
+    }
+    ell_cone(uc, P->D[3 * c], P->D[3 * c + 1], mu[3 * c], &s, g, h);
+    d += g[0] * vc[0] + g[1] * vc[1] + g[2] * vc[2];
+  }
+  return d;
+}
+
+/* Exact line search along p (phi is convex, phi' continuous and increasing):
+ * bracket the root of phi' by doubling from alpha = 1, then bisect until the
+ * bracket cannot shrink in double precision. */
+static double ell_line_search(const problem *P, const double *mu, const double *a,
+                              const double *p) {
+  double lo = 0.0, hi = 1.0;
+  for (int k = 0; k < 200 && ell_dphi(P, mu, a, p, hi) < 0.0; ++k) {
+    lo = hi;
+    hi *= 2.0;
+  }
+  for (int k = 0; k < 400; ++k) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (ell_dphi(P, mu, a, p, mid) < 0.0) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+double oracle_ell_line_search(int nv, int m, const double *M, const double *J,
+                              const double *qfrc, const double *aref,
+                              const double *D, const double *mu, const double *a,
+                              const double *p) {
+  problem P = {nv, m, M, J, qfrc, aref, D};
+  return ell_line_search(&P, mu, a, p);
+}
+
+/* Objective of Eq. 5 with the round cone at a (a0 = M^-1 qfrc recomputed). */
+double oracle_ell_objective(int nv, int m, const double *M, const double *J,
+                            const double *qfrc, const double *aref,
+                            const double *D, const double *mu, const double *a) {
+  problem P = {nv, m, M, J, qfrc, aref, D};
+  double *w = (double *)calloc((size_t)(nv * nv + 5 * nv + 14 * m + 8), sizeof(double));
+  uint8_t *zone = (uint8_t *)calloc((size_t)m + 1, 1);
+  double *H = w, *a0 = H + nv * nv, *d = a0 + nv, *Ma = d + nv, *Jtf = Ma + nv;
+  double *r = Jtf + nv, *u = r + nv, *grad = u + m, *hessb = grad + m;
+  memcpy(H, M, sizeof(double) * nv * nv);
+  double v = NAN;
+  if (!chol(nv, H)) {
+    memcpy(a0, qfrc, sizeof(double) * nv);
+    chol_solve(nv, H, a0);
+    v = 0.0;
+    for (int j = 0; j < nv; ++j) d[j] = a[j] - a0[j];
+    for (int j = 0; j < nv; ++j)
+      for (int k = 0; k < nv; ++k) v += 0.5 * d[j] * M[j * nv + k] * d[k];
+    ell_residual(&P, mu, a, u, zone, grad, hessb, Ma, Jtf, r, &v);
+  }
+  free(w);
+  free(zone);
+  return v;
+}
+
+/* Newton on the stationarity residual with the round cone (Eqs. 6-10): from
+ * a0 = M^-1 qfrc, p = -H^-1 r with the block Hessians, exact line search,
+ * stop at ||r||_inf <= tol * scale or at a step below double-precision
+ * resolution of a (64 eps |a|_inf; Newton converges quadratically, so a is
+ * then at its double-precision fixed point).  zone (out, m) holds each contact's zone
+ * on its three rows at the returned a.  Returns a status code. */
+int oracle_ell_solve(int nv, int m, const double *M, const double *J,
+                     const double *qfrc, const double *aref, const double *D,
+                     const double *mu, double tol, int max_iter, double *a,
+                     uint8_t *zone, int *iters) {
+  *iters = 0;
+  if (nv < 1 || m < 0 || m % 3) return OR_BADSHAPE;
+  problem P = {nv, m, M, J, qfrc, aref, D};
+  double *w = (double *)calloc((size_t)(nv * nv + 5 * nv + 14 * m + 8), sizeof(double));
+  double *H = w, *p = H + nv * nv, *Ma = p + nv, *Jtf = Ma + nv, *r = Jtf + nv;
+  double *u = r + nv, *grad = u + m, *hessb = grad + m;
+  int status = OR_MAXITER;
+  memcpy(H, M, sizeof(double) * nv * nv);
+  if (chol(nv, H)) { status = OR_CHOLFAIL; goto done; }
+  memcpy(a, qfrc, sizeof(double) * nv);
+  chol_solve(nv, H, a);
+  for (int k = 0;; ++k) {
+    const double scale = ell_residual(&P, mu, a, u, zone, grad, hessb, Ma, Jtf, r, NULL);
+    const double rn = inf_norm(nv, r);
+    if (!isfinite(rn) || !isfinite(scale)) { status = OR_NONFINITE; break; }
+    if (rn <= tol * scale) { status = OR_OK; break; }
+    if (k >= max_iter) { status = OR_MAXITER; break; }
+    ell_newton_matrix(&P, hessb, H);
+    if (chol(nv, H)) { status = OR_CHOLFAIL; break; }
+    for (int j = 0; j < nv; ++j) p[j] = -r[j];
+    chol_solve(nv, H, p);
+    double ptr = 0.0;
+    for (int j = 0; j < nv; ++j) ptr += p[j] * r[j];
+    if (!(ptr < 0.0)) { status = OR_NOPROGRESS; break; }
+    const double alpha = ell_line_search(&P, mu, a, p);
+    double step = 0.0;
+    for (int j = 0; j < nv; ++j) {
+      const double dj = alpha * p[j];
+      a[j] += dj;
+      if (fabs(dj) > step) step = fabs(dj);
+    }
+    *iters = k + 1;
+    /* a step below double-precision resolution: the residual has reached its
+     * rounding floor (the middle zone's gradient cancels large terms) */
+    if (step <= 64.0 * 2.220446049250313e-16 * inf_norm(nv, a)) {
+      ell_residual(&P, mu, a, u, zone, grad, hessb, Ma, Jtf, r, NULL);
+      status = OR_OK;
+      break;
+    }
+  }
+done:
+  free(w);
+  return status;
+}
+
+/* IFT adjoint (Eq. 17) with the round cone at the point a: H w = g with
+ * H = M + sum_c J_c^T hess_c J_c; dqfrc = w; daref_c = hess_c (J w)_c;
+ * dJ = -(grad w^T + daref a^T); dM = -(w a^T + a w^T)/2 (symmetric M);
+ * and the cone parameters, dL/dtheta_c = -(J w)_c . d grad_c / d theta_c:
+ * dD[3c] for D_N, dD[3c+1] for D_T (dD[3c+2] = 0: not read), dmu[3c] for mu
+ * (the other rows 0).  Any output after dJ may be NULL. */
+int oracle_ell_adjoint(int nv, int m, const double *M, const double *J,
+                       const double *qfrc, const double *aref, const double *D,
+                       const double *mu, const double *a, const double *g,
+                       double *dqfrc, double *daref, double *dJ, double *dM,
+                       double *dD, double *dmu, uint8_t *zone) {
+  if (nv < 1 || m < 0 || m % 3) return OR_BADSHAPE;
+  problem P = {nv, m, M, J, qfrc, aref, D};
+  const int nc = m / 3;
+  double *w = (double *)calloc((size_t)(nv * nv + 5 * nv + 14 * m + 8), sizeof(double));
+  double *H = w, *Ma = H + nv * nv, *Jtf = Ma + nv, *r = Jtf + nv;
+  double *u = r + nv, *grad = u + m, *hessb = grad + m, *v = hessb + 9 * (m / 3) + 3;
+  int status = 0;
+  ell_residual(&P, mu, a, u, zone, grad, hessb, Ma, Jtf, r, NULL);
+  ell_newton_matrix(&P, hessb, H);
+  if (chol(nv, H)) { status = OR_CHOLFAIL; goto done; }
+  memcpy(dqfrc, g, sizeof(double) * nv);
+  chol_solve(nv, H, dqfrc);
+  for (int i = 0; i < m; ++i) {
+    double x = 0.0;
+    for (int k = 0; k < nv; ++k) x += J[i * nv + k] * dqfrc[k];
+    v[i] = x;
+  }
+  for (int c = 0; c < nc; ++c)
+    for (int q = 0; q < 3; ++q) {
+      double x = 0.0;
+      for (int p = 0; p < 3; ++p) x += hessb[9 * c + 3 * q + p] * v[3 * c + p];
+      daref[3 * c + q] = x;
+    }
+  for (int i = 0; i < m; ++i)
+    for (int k = 0; k < nv; ++k) dJ[i * nv + k] = -(grad[i] * dqfrc[k] + daref[i] * a[k]);
+  if (dM)
+    for (int j = 0; j < nv; ++j)
+      for (int k = 0; k < nv; ++k)
+        dM[j * nv + k] = -0.5 * (dqfrc[j] * a[k] + a[j] * dqfrc[k]);
+  if (dD || dmu) {
+    for (int c = 0; c < nc; ++c) {
+      const double DN = D[3 * c], DT = D[3 * c + 1], f = mu[3 * c];
+      const double *uc = u + 3 * c, *vc = v + 3 * c;
+      double gN[3] = {0, 0, 0}, gT[3] = {0, 0, 0}, gm[3] = {0, 0, 0};
+      const double t = sqrt(uc[1] * uc[1] + uc[2] * uc[2]);
+      if (zone[3 * c] == 2) {
+        gN[0] = uc[0];
+        gT[1] = uc[1];
+        gT[2] = uc[2];
+      } else if (zone[3 * c] == 1) {
+        const double den = DT + f * f * DN;
+        const double Dm = DN * DT / den, phi = f * t - uc[0];
+        const double h1 = t > 0.0 ? uc[1] / t : 0.0, h2 = t > 0.0 ? uc[2] / t : 0.0;
+        const double gv[3] = {-1.0, f * h1, f * h2};
+        const double dDN = DT * DT / (den * den), dDT = f * f * DN * DN / (den * den);
+        const double dmu_ = -2.0 * f * DN * DN * DT / (den * den);
+        for (int q = 0; q < 3; ++q) {
+          gN[q] = dDN * phi * gv[q];
+          gT[q] = dDT * phi * gv[q];
+          gm[q] = dmu_ * phi * gv[q] + Dm * t * gv[q];
+        }
+        gm[1] += Dm * phi * h1;
+        gm[2] += Dm * phi * h2;
+      }
+      if (dD) {
+        dD[3 * c] = -(vc[0] * gN[0] + vc[1] * gN[1] + vc[2] * gN[2]);
+        dD[3 * c + 1] = -(vc[0] * gT[0] + vc[1] * gT[1] + vc[2] * gT[2]);
+        dD[3 * c + 2] = 0.0;
+      }
+      if (dmu) {
+        dmu[3 * c] = -(vc[0] * gm[0] + vc[1] * gm[1] + vc[2] * gm[2]);
+        dmu[3 * c + 1] = dmu[3 * c + 2] = 0.0;
+      }
+    }
+  }
+done:
+  free(w);
+  return status;
+}
+
 /* ---- unrolled reverse-mode derivative (the paper's comparison) --------- */
 
 /* Derivative of L = g^T a_K through the executed trace of at most K Newton

@@ -13,7 +13,13 @@ reading of the cone term):
 * ``qfrc`` nv smooth generalised force (tau - c in Eq. 1),
 * ``aref`` m reference accelerations,
 * ``D``    m positive row stiffnesses (D = R^-1 in Eq. 4),
-* ``g``    nv loss cotangent dL/da (loss L = g^T a).
+* ``g``    nv loss cotangent dL/da (loss L = g^T a),
+* ``mu``   (round-cone workloads only) m friction coefficients, one value per
+           contact repeated on its three rows.
+
+Round (elliptic) cone workloads use three rows per contact (normal, two
+tangents); D holds D_N on the normal row and one tangential D_T on both
+tangent rows, and mu_c ~ U(0.2, 1.2).
 
 Distributions: J, qfrc, aref, g ~ N(0,1); D_i = 10^U(2,5).  M is either
 ``L L^T + 0.1 I`` with Gaussian L (the tiny workload) or ``Q diag(lambda) Q^T``
@@ -54,6 +60,7 @@ class Workload:
     D: np.ndarray             # float32[total_r]
     g: np.ndarray             # float32[total_v]
     params: dict
+    mu: np.ndarray | None = None  # float32[total_r], round-cone workloads only
 
     @property
     def n(self) -> int:
@@ -73,13 +80,16 @@ class Workload:
         nv, m = int(e["nv"]), int(e["m"])
         oM, oJ, ov, orr = (int(e["off_M"]), int(e["off_J"]), int(e["off_v"]),
                            int(e["off_r"]))
-        return dict(
+        out = dict(
             nv=nv, m=m,
             M=self.M[oM:oM + nv * nv].reshape(nv, nv),
             J=self.J[oJ:oJ + m * nv].reshape(m, nv),
             qfrc=self.qfrc[ov:ov + nv], aref=self.aref[orr:orr + m],
             D=self.D[orr:orr + m], g=self.g[ov:ov + nv],
         )
+        if self.mu is not None:
+            out["mu"] = self.mu[orr:orr + m]
+        return out
 
     def subset(self, idx) -> "Workload":
         """Re-pack the instances ``idx`` (in that order) into a new workload."""
@@ -128,6 +138,8 @@ def pack(parts, name="custom", params=None) -> Workload:
     g = np.zeros(tv, np.float32)
     aref = np.zeros(tr, np.float32)
     D = np.zeros(tr, np.float32)
+    has_mu = bool(parts) and all("mu" in p for p in parts)
+    mu = np.zeros(tr, np.float32) if has_mu else None
     for b, p in enumerate(parts):
         e = inst[b]
         nv, m = int(e["nv"]), int(e["m"])
@@ -139,7 +151,9 @@ def pack(parts, name="custom", params=None) -> Workload:
         g[ov:ov + nv] = np.asarray(p.get("g", np.zeros(nv)), np.float32)
         aref[orr:orr + m] = np.asarray(p["aref"], np.float32)
         D[orr:orr + m] = np.asarray(p["D"], np.float32)
-    return Workload(name, inst, M, J, qfrc, aref, D, g, params or {})
+        if has_mu:
+            mu[orr:orr + m] = np.asarray(p["mu"], np.float32)
+    return Workload(name, inst, M, J, qfrc, aref, D, g, params or {}, mu)
 
 
 def _mass_matrices(rng, n, nv, kind, cond):
@@ -159,14 +173,18 @@ def _mass_matrices(rng, n, nv, kind, cond):
 
 
 def generate(name, n, nv, contacts, *, seed, m_kind="spectrum", cond=1e3,
-             d_lo=2.0, d_hi=5.0) -> Workload:
+             d_lo=2.0, d_hi=5.0, cone="pyramid", mu_lo=0.2, mu_hi=1.2) -> Workload:
     """Draw ``n`` instances with fixed ``nv`` and per-instance contact counts.
 
     ``contacts`` is an int (every instance) or an array of length n.
+    ``cone`` is "pyramid" (four rows per contact) or "elliptic" (three rows
+    per contact with per-contact D_N, D_T and mu).
     """
+    if cone not in ("pyramid", "elliptic"):
+        raise ValueError(cone)
     rng = np.random.Generator(np.random.PCG64(seed))
     nc = np.broadcast_to(np.asarray(contacts, dtype=np.int64), (n,)).copy()
-    ms = ROWS_PER_CONTACT * nc
+    ms = (ROWS_PER_CONTACT if cone == "pyramid" else 3) * nc
     inst, tM, tJ, tv, tr = layout(np.full(n, nv), ms)
     Ms = _mass_matrices(rng, n, nv, m_kind, cond).astype(np.float32)
     total_rows = int(ms.sum())
@@ -199,8 +217,20 @@ def generate(name, n, nv, contacts, *, seed, m_kind="spectrum", cond=1e3,
     jdst = (inst["off_J"][inst_of_row] + local_row * nv)[:, None] + np.arange(nv)[None, :]
     J[jdst.ravel()] = Jrows.ravel()
     params = dict(n=n, nv=nv, seed=seed, m_kind=m_kind, cond=cond,
-                  d_range=(10 ** d_lo, 10 ** d_hi))
-    return Workload(name, inst, M, J, qfrc, aref, D, g, params)
+                  d_range=(10 ** d_lo, 10 ** d_hi), cone=cone)
+    mu = None
+    if cone == "elliptic":
+        # drawn after everything else, so the other arrays match the draws
+        # of a pyramid workload with the same seed and row count
+        ncon = total_rows // 3
+        Dc = (10.0 ** rng.uniform(d_lo, d_hi, (ncon, 2))).astype(np.float32)
+        muc = rng.uniform(mu_lo, mu_hi, ncon).astype(np.float32)
+        Drow = np.repeat(Dc, [1, 2], axis=1).reshape(-1)       # D_N, D_T, D_T
+        D[rdst] = Drow
+        mu = np.zeros(tr, np.float32)
+        mu[rdst] = np.repeat(muc, 3)
+        params["mu_range"] = (mu_lo, mu_hi)
+    return Workload(name, inst, M, J, qfrc, aref, D, g, params, mu)
 
 
 # The five workloads (sizes and distributions of the paper-scale settings):
@@ -234,6 +264,17 @@ def nv96(n=2048, seed=SEEDS["nv96"]):
 
 def nc256(n=256, seed=SEEDS["nc256"] + 1):
     return generate("nc256", n, 18, 256, seed=seed, cond=1e3)
+
+
+def quadruped_elliptic(n=32768, seed=SEEDS["quadruped"], max_contacts=32):
+    """The quadruped batch with MuJoCo's round cone: three rows per contact."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    nc = rng.integers(0, max_contacts + 1, size=n)
+    return generate("quadruped_elliptic", n, 18, nc, seed=seed, cond=1e3, cone="elliptic")
+
+
+def franka_elliptic(n=8192, seed=SEEDS["franka"]):
+    return generate("franka_elliptic", n, 9, 16, seed=seed, cond=1e3, cone="elliptic")
 
 
 def serve_stream(n_requests=200_000, rate=50_000.0, seed=SEEDS["serve"],
