@@ -287,6 +287,33 @@ void cs_plan_destroy(cs_plan* plan);
 int cs_autotune_cache_dump(char* buf, size_t len);
 int cs_autotune_cache_load(const char* text);
 
+/* ---- MuJoCo's round Coulomb cone --------------------------------------- */
+
+/* cs_solve_fused with the round cone the paper keeps (Eq. 2) instead of
+ * pyramid rows.  Each contact c owns three rows of J, aref and D: 3c (normal)
+ * and 3c+1, 3c+2 (tangents); every instance's m must be a multiple of 3
+ * (CS_ST_BADSHAPE otherwise).  Its cost is the weighted distance of
+ * u = J a - aref to the dual cone (Eqs. 3-5),
+ *   s_c(u) = min over z_N >= mu_c |z_T| of 1/2 (u - z)^T diag(D_N, D_T, D_T) (u - z),
+ * with D_N = D[3c], D_T = D[3c+1] (one tangential stiffness; D[3c+2] is not
+ * read) and mu_c = mu[3c] (mu: device, total_r floats laid out like D; only
+ * the normal rows are read).  The solve is Newton on r = M a - qfrc +
+ * J^T grad s with H = M + sum_c J_c^T hess_c J_c and an exact line search on
+ * the convex phi(alpha); the adjoint (Eq. 17) at the returned a writes
+ * dqfrc = w, daref = hess (J w) per contact, dJ = -(grad s w^T + daref a^T)
+ * and, where non-NULL, dM (symmetric M, as cs_solve_fused_theta), dD
+ * (dL/dD_N on row 3c, dL/dD_T on row 3c+1, 0 on 3c+2) and dmu (dL/dmu_c on
+ * row 3c, 0 on the tangent rows).  Sizes: one warp per instance (nv_max <= 32,
+ * m_max <= 256), CS_EUNSUPPORTED otherwise.  Workspace, order and errors as
+ * for cs_solve_fused. */
+int cs_solve_fused_elliptic(const cs_batch* batch, const cs_options* opt,
+                            const float* mu, const float* g,
+                            const int32_t* order, float* a, float* dqfrc,
+                            float* daref, float* dJ, float* dM, float* dD,
+                            float* dmu, int32_t* status, int32_t* iters,
+                            void* workspace, size_t workspace_bytes,
+                            void* stream);
+
 /* ---- unrolled differentiation (the paper's comparison) ---------------- */
 
 /* The sensitivity the paper sets against the IFT adjoint (Section III-E):

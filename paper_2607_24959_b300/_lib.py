@@ -102,6 +102,12 @@ _SIGS = {
                                               c_void_p, c_void_p, c_void_p, c_void_p,
                                               c_void_p, c_void_p]),
     "cs_fused_workspace_bytes": (c_size_t, [c_int32]),
+    "cs_solve_fused_elliptic": (ctypes.c_int, [ctypes.POINTER(CsBatch),
+                                               ctypes.POINTER(CsOptions), c_void_p, c_void_p,
+                                               c_void_p, c_void_p, c_void_p, c_void_p,
+                                               c_void_p, c_void_p, c_void_p, c_void_p,
+                                               c_void_p, c_void_p, c_void_p, c_size_t,
+                                               c_void_p]),
     "cs_unrolled_trace_floats": (c_size_t, [ctypes.POINTER(CsBatch), c_int32]),
     "cs_unrolled_mask_bytes": (c_size_t, [ctypes.POINTER(CsBatch), c_int32]),
     "cs_unrolled_fwd": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),

@@ -301,6 +301,41 @@ def solve_fused(batch: DeviceBatch, g, order=None, tol=DEFAULT_TOL,
     return out
 
 
+@dataclasses.dataclass
+class EllipticOut:
+    """Outputs of the round-cone fused solve (packed like the batch)."""
+
+    fused: FusedOut        # a, dqfrc, daref, dJ, status, iters, workspace, dM, dD
+    dmu: torch.Tensor
+
+
+ELLIPTIC_MAX_ITER = 100   # the round cone's middle zone needs more Newton steps
+
+
+def solve_fused_elliptic(batch: DeviceBatch, g, mu, order=None, tol=DEFAULT_TOL,
+                         max_iter=ELLIPTIC_MAX_ITER, warps_per_block=0,
+                         out: EllipticOut | None = None) -> EllipticOut:
+    """Fused forward + adjoint with the round Coulomb cone
+    (cs_solve_fused_elliptic): three rows per contact, mu per contact on its
+    normal row; writes every parameter gradient including dM, dD and dmu."""
+    lib = _lib.load()
+    if out is None:
+        out = EllipticOut(alloc_fused(batch, theta=True),
+                          torch.empty(max(batch.total_r, 1), dtype=torch.float32,
+                                      device=batch.M.device))
+    f = out.fused
+    b = batch.cstruct()
+    o = options(tol, max_iter, True, warps_per_block)
+    g = g.contiguous()
+    mu = mu.contiguous()
+    _lib.check(lib.cs_solve_fused_elliptic(
+        ctypes.byref(b), ctypes.byref(o), _ptr(mu), _ptr(g), _ptr(order), _ptr(f.a),
+        _ptr(f.dqfrc), _ptr(f.daref), _ptr(f.dJ), _ptr(f.dM), _ptr(f.dD), _ptr(out.dmu),
+        _ptr(f.status), _ptr(f.iters), _ptr(f.workspace), f.workspace.numel(), _stream()),
+        "cs_solve_fused_elliptic")
+    return out
+
+
 def solve_fused_static(batch: DeviceBatch, g, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
                        warps_per_block=0, cost_ordered=True, out: FusedOut | None = None):
     """solve_fused without any device allocation by the library: the claim
