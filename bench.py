@@ -403,6 +403,8 @@ def run_gpu(args):
         line["serve"] = run_serve(args)
     if not args.no_memory and world == 1:
         line["adjoint_memory"] = run_memory(args)
+    if not args.no_elliptic and world == 1:
+        line["elliptic"] = run_elliptic(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, max_instances=args.cpu_sample)
     print(json.dumps(line), flush=True)
@@ -511,6 +513,48 @@ def run_memory(args):
     return out
 
 
+def run_elliptic(args):
+    """The same workload shape with MuJoCo's round cone (three rows per
+    contact, Eqs. 2-5): one fused launch of cs_solve_fused_elliptic per step
+    over the 32768-instance batch, cost-ordered claims, CUDA-event timed on
+    its stream after warm-up."""
+    import torch
+    from paper_2607_24959_b300 import solver, workloads as W
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    w = W.quadruped_elliptic()
+    batch = solver.DeviceBatch.from_workload(w, dev)
+    g = torch.from_numpy(w.g).to(dev)
+    mu = torch.from_numpy(w.mu).to(dev)
+    order = torch.from_numpy(solver.cost_order(w.inst)).to(dev)
+    out = solver.solve_fused_elliptic(batch, g, mu, order=order, tol=args.tol)
+    stream = torch.cuda.Stream(device=dev)
+    steps = max(3, min(args.steps, 50))
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            solver.solve_fused_elliptic(batch, g, mu, order=order, tol=args.tol, out=out)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            solver.solve_fused_elliptic(batch, g, mu, order=order, tol=args.tol, out=out)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = out.fused.status.cpu().numpy()[:w.n]
+    it = out.fused.iters.cpu().numpy()[:w.n]
+    res = {"metric": "round-cone fwd+IFT-adjoint solves/s (all parameter gradients)",
+           "value": w.n / (ms / 1e3), "unit": "solves/s", "ms_per_step": ms, "steps": steps,
+           "config": {"workload": "quadruped_elliptic", "instances": w.n, "nv": 18,
+                      "contacts": "U{0..32}, 3 rows each", "mu": "U(0.2, 1.2)"},
+           "status_counts": np.bincount(st, minlength=6).tolist(),
+           "iters_mean": float(it.mean()), "iters_max": int(it.max()),
+           "gpu_launches_per_step": 1}
+    del out, batch
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_e2e(args, w, batch, dev, kw, world):
     """Same metric through the public API with pinned host buffers: every step
     copies its inputs host->device and its results device->host
@@ -556,6 +600,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=32768)
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-elliptic", action="store_true",
+                    help="skip the round-cone throughput leg")
     ap.add_argument("--no-memory", action="store_true",
                     help="skip the IFT vs unrolled differentiation memory sweeps")
     ap.add_argument("--e2e-chunks", type=int, default=8)

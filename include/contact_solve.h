@@ -183,6 +183,21 @@ int cs_solve_fused(const cs_batch* batch, const cs_options* opt,
                    int32_t* iters, void* workspace, size_t workspace_bytes,
                    void* stream);
 
+/* cs_solve_fused with the nonlinear conjugate-gradient forward solver, the
+ * other iteration MJX offers for the same objective (Section III-B): search
+ * directions preconditioned by M^-1 with the Polak-Ribiere+ beta (restarted
+ * when the active set changes and every nv steps) and the exact line search
+ * of Eq. 10; opt->max_iter caps the CG steps (many more than Newton needs).
+ * The adjoint is the same IFT rule at the returned point (Eq. 17): it does
+ * not depend on the path taken to a* (Eq. 14).  One warp per instance only
+ * (nv_max <= 32, m_max <= 256), CS_EUNSUPPORTED otherwise; arguments and
+ * errors as for cs_solve_fused. */
+int cs_solve_fused_ncg(const cs_batch* batch, const cs_options* opt,
+                       const float* g, const int32_t* order, float* a,
+                       float* dqfrc, float* daref, float* dJ, int32_t* status,
+                       int32_t* iters, void* workspace, size_t workspace_bytes,
+                       void* stream);
+
 /* cs_solve_fused that also writes dM and dD as cs_solve_adjoint_theta does
  * (either may be NULL). */
 int cs_solve_fused_theta(const cs_batch* batch, const cs_options* opt,

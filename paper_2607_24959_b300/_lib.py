@@ -102,6 +102,10 @@ _SIGS = {
                                               c_void_p, c_void_p, c_void_p, c_void_p,
                                               c_void_p, c_void_p]),
     "cs_fused_workspace_bytes": (c_size_t, [c_int32]),
+    "cs_solve_fused_ncg": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
+                                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                          c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                                          c_void_p]),
     "cs_solve_fused_elliptic": (ctypes.c_int, [ctypes.POINTER(CsBatch),
                                                ctypes.POINTER(CsOptions), c_void_p, c_void_p,
                                                c_void_p, c_void_p, c_void_p, c_void_p,

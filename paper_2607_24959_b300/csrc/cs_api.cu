@@ -246,6 +246,42 @@ int cs_solve_fused(const cs_batch* batch, const cs_options* opt, const float* g,
                               status, iters, workspace, workspace_bytes, stream);
 }
 
+int cs_solve_fused_ncg(const cs_batch* batch, const cs_options* opt, const float* g,
+                       const int32_t* order, float* a, float* dqfrc, float* daref, float* dJ,
+                       int32_t* status, int32_t* iters, void* workspace, size_t workspace_bytes,
+                       void* stream) {
+  int rc = check_batch_shapes(batch, opt);
+  if (rc != CS_OK || batch->n == 0) return rc;
+  if (!uses_warp_kernel(batch->nv_max, batch->m_max))
+    return set_error(CS_EUNSUPPORTED,
+                     "the conjugate-gradient solve runs one warp per instance: nv_max <= 32 "
+                     "and m_max <= 256 (got %d, %d)",
+                     batch->nv_max, batch->m_max);
+  if (!g || !a || !dqfrc || !status || !iters || (batch->m_max > 0 && (!daref || !dJ)))
+    return set_error(CS_EINVAL, "g and the output arrays must not be NULL");
+  if (!workspace || workspace_bytes < cs_fused_workspace_bytes(batch->n) ||
+      (reinterpret_cast<uintptr_t>(workspace) & 15))
+    return set_error(CS_EINVAL, "workspace must be >= %zu bytes and 16-byte aligned",
+                     cs_fused_workspace_bytes(batch->n));
+  csk::Params P = make_params(batch, opt);
+  P.g = g;
+  P.a = a;
+  P.dqfrc = dqfrc;
+  P.daref = daref;
+  P.dJ = dJ;
+  P.status = status;
+  P.iters = iters;
+  P.counter = reinterpret_cast<int32_t*>(workspace);
+  P.order = order;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return cuda_error(e, "cs_solve_fused_ncg counter reset");
+  LaunchCfg cfg;
+  cfg.warps_per_block = opt->warps_per_block;
+  e = launch_warp(csk::MODE_FUSED_NCG, batch->nv_max, batch->m_max, P, cfg, s, nullptr);
+  return e == cudaSuccess ? CS_OK : launch_error(e, "cs_solve_fused_ncg launch");
+}
+
 int cs_solve_fused_theta(const cs_batch* batch, const cs_options* opt, const float* g,
                          const int32_t* order, float* a, float* dqfrc, float* daref, float* dJ,
                          float* dM, float* dD, int32_t* status, int32_t* iters,

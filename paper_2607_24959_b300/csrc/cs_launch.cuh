@@ -66,6 +66,7 @@ cudaError_t launch_nv(int mode, int mt, const csk::Params& P, const LaunchCfg& c
   switch (mode) {
     case csk::MODE_FWD: return launch_mt<NV, csk::MODE_FWD>(mt, P, cfg, s, info);
     case csk::MODE_ADJ: return launch_mt<NV, csk::MODE_ADJ>(mt, P, cfg, s, info);
+    case csk::MODE_FUSED_NCG: return launch_mt<NV, csk::MODE_FUSED_NCG>(mt, P, cfg, s, info);
     default: return launch_mt<NV, csk::MODE_FUSED>(mt, P, cfg, s, info);
   }
 }

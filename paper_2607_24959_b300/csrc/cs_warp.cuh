@@ -138,7 +138,7 @@ struct Params {
   const int32_t* order;     // claim order or null
 };
 
-enum Mode { MODE_FWD = 0, MODE_ADJ = 1, MODE_FUSED = 2 };
+enum Mode { MODE_FWD = 0, MODE_ADJ = 1, MODE_FUSED = 2, MODE_FUSED_NCG = 3 };
 
 template <int NV, int MT>
 struct WarpSolver {
@@ -590,6 +590,15 @@ struct WarpSolver {
   // lane.  phi'(alpha) = c0 + alpha p^T M p + sum_i D_i s_i min(jar_i + alpha s_i, 0)
   // with c0 = p^T (M a - qfrc) and s = J p; phi' is continuous, piecewise
   // linear and strictly increasing.  Also leaves s_r = J p.
+  //
+  // kDiff evaluates the same phi' in difference form,
+  //   phi'(alpha) = p^T r + alpha (p^T M p + sum_{active at alpha} D s^2)
+  //                 - sum_{leaving} D s jar + sum_{entering} D s jar,
+  // with p^T r compensated: nothing cancels, so a directional derivative far
+  // below the size of p^T (M a - qfrc) and of the contact terms (conjugate
+  // gradients near a*) is still resolved.  Newton steps have their root near
+  // alpha = 1 and use the plain form.
+  template <bool kDiff = false>
   __device__ __forceinline__ float line_search(float p, float* dfmax, bool* crossed) {
     put_vec(V_P, p);
     const float* Jm = Js() + lane * G::JS;
@@ -607,7 +616,14 @@ struct WarpSolver {
       Mp = __fmaf_rn(Mr[k], pk, Mp);
     }
     const float pMp = warp_sum(lane < NV ? p * Mp : 0.f);
-    const float c0 = warp_sum(p * maq);
+    float c0;
+    if (kDiff) {
+      const float prh = __fmul_rn(p, r);
+      const float prl = __fmaf_rn(p, rlo, __fmaf_rn(p, r, -prh));
+      c0 = warp_sum(prh) + warp_sum(prl);
+    } else {
+      c0 = warp_sum(p * maq);
+    }
     float bp[MT];
 #pragma unroll
     for (int t = 0; t < MT; ++t)
@@ -624,7 +640,12 @@ struct WarpSolver {
         if (row_valid(t)) {
           const float u = __fmaf_rn(alpha, s_r[t], jar_r[t]);
           const float ds = D_r[t] * s_r[t];
-          if (u < 0.f) {
+          if (kDiff) {
+            const bool on0 = (act_bits >> t) & 1u;
+            if (u < 0.f) cs = __fmaf_rn(ds, s_r[t], cs);
+            if (on0 && !(u < 0.f)) sum = __fmaf_rn(-ds, jar_r[t], sum);
+            if (!on0 && u < 0.f) sum = __fmaf_rn(ds, jar_r[t], sum);
+          } else if (u < 0.f) {
             sum = __fmaf_rn(ds, u, sum);
             cs = __fmaf_rn(ds, s_r[t], cs);
           }
@@ -632,7 +653,7 @@ struct WarpSolver {
       }
       sum = warp_sum(sum);
       cs = warp_sum(cs);
-      const float d = c0 + alpha * pMp + sum;
+      const float d = kDiff ? c0 + alpha * (pMp + cs) + sum : c0 + alpha * pMp + sum;
       if (d == 0.f) break;
       float an = alpha - d / (pMp + cs), x0, x1;
       if (d < 0.f) {
@@ -749,6 +770,68 @@ struct WarpSolver {
       p_prev = p;
       zr_prev = zr;
       precise = precise || !crossed;
+    }
+  }
+
+  // ------------------------------------------- nonlinear conjugate gradients
+  // The other forward solver MJX offers: conjugate directions on the same
+  // objective (Eq. 5), preconditioned by M^-1 (the factor of M stays in
+  // Ls()), the Polak-Ribiere+ beta (which resets itself when the gradient
+  // turns; a non-descent direction restarts from -M^-1 r), and the exact line
+  // search of Eq. 10.  Residuals are compensated throughout (CG steps keep
+  // crossing breakpoints, so the plain phase of forward() would never end).
+  // It stops on the residual test, or once the residual has not halved over
+  // 4 nv + 20 steps while below 1e-5 of its scale (FP32 conjugacy is lost at
+  // cond(M^-1 H) ~ 1e6 and the iteration only creeps); a short CG step alone
+  // says nothing about the distance to a*.  The adjoint does not depend on
+  // how a* was reached (Eq. 14): run<MODE_FUSED_NCG> rebuilds H(a*).
+  __device__ __forceinline__ int forward_ncg(const Params& P, int* iters) {
+    *iters = 0;
+    if (!factor_M()) return CS_ST_CHOLFAIL;
+    fmask_valid = false;  // Ls() holds chol(M), not a factor of H
+    ah = chol_solve(qf);
+    al = 0.f;
+    bool have_prev = false;
+    float d_prev = 0.f, r_prev = 0.f, zr_prev = 1.f, best = CUDART_INF_F;
+    int since_best = 0;
+#pragma unroll 1
+    for (int k = 0;; ++k) {
+      float scale;
+      bool bad;
+      const float rmax = residual(&scale, &bad, true);
+      if (bad) return CS_ST_NONFINITE;
+      if (rmax <= P.tol * scale) return CS_ST_OK;
+      if (rmax < 0.5f * best) {
+        best = rmax;
+        since_best = 0;
+      } else if (++since_best > 4 * nv + 20 && rmax <= 1e-5f * scale) {
+        return CS_ST_OK;
+      }
+      if (k >= P.max_iter) return CS_ST_MAXITER;
+      const float z = chol_solve(r);
+      const float zr = warp_sum(z * r);
+      float beta = 0.f;
+      if (have_prev && zr_prev > 0.f) beta = fmaxf(warp_sum(z * (r - r_prev)) / zr_prev, 0.f);
+      float d = __fmaf_rn(beta, d_prev, -z);
+      float dtr = warp_sum(d * r);
+      if (!(dtr < 0.f) && beta != 0.f) {
+        d = -z;
+        dtr = -zr;
+      }
+      const float amax = warp_max(fabsf(ah));
+      if (!(dtr < 0.f)) {
+        const float dm = warp_max(fabsf(d));
+        return (dm <= kStepTol * amax) ? CS_ST_OK : CS_ST_NOPROGRESS;
+      }
+      float dfm;
+      bool crossed;
+      const float alpha = line_search<true>(d, &dfm, &crossed);
+      add_to_pair(ah, al, alpha * d);
+      *iters = k + 1;
+      d_prev = d;
+      r_prev = r;
+      zr_prev = zr;
+      have_prev = true;
     }
   }
 
@@ -921,17 +1004,17 @@ struct WarpSolver {
       }
       return;
     }
-    if (MODE == MODE_FWD || MODE == MODE_FUSED) {
-      gj = (MODE == MODE_FUSED && lane < nv) ? __ldg(P.g + e.off_v + lane) : 0.f;
+    if (MODE == MODE_FWD || MODE == MODE_FUSED || MODE == MODE_FUSED_NCG) {
+      gj = (MODE != MODE_FWD && lane < nv) ? __ldg(P.g + e.off_v + lane) : 0.f;
       int iters = 0;
-      const int st = forward(P, &iters);
+      const int st = (MODE == MODE_FUSED_NCG) ? forward_ncg(P, &iters) : forward(P, &iters);
       if (lane < nv) P.a[e.off_v + lane] = ah;
       if (lane == 0) {
         P.status[b] = st;
         P.iters[b] = iters;
       }
       if (st == CS_ST_CHOLFAIL || st == CS_ST_NONFINITE) {
-        if (MODE == MODE_FUSED) zero_grads(P, e);
+        if (MODE != MODE_FWD) zero_grads(P, e);
         return;
       }
       if (MODE == MODE_FWD) {

@@ -301,6 +301,26 @@ def solve_fused(batch: DeviceBatch, g, order=None, tol=DEFAULT_TOL,
     return out
 
 
+NCG_MAX_ITER = 5000   # conjugate-gradient steps (Newton needs about ten)
+
+
+def solve_fused_ncg(batch: DeviceBatch, g, order=None, tol=DEFAULT_TOL, max_iter=NCG_MAX_ITER,
+                    warps_per_block=0, out: FusedOut | None = None) -> FusedOut:
+    """Fused forward + adjoint with the nonlinear conjugate-gradient forward
+    solver (cs_solve_fused_ncg); the adjoint is the same IFT rule."""
+    lib = _lib.load()
+    if out is None:
+        out = alloc_fused(batch)
+    b = batch.cstruct()
+    o = options(tol, max_iter, True, warps_per_block)
+    g = g.contiguous()
+    _lib.check(lib.cs_solve_fused_ncg(
+        ctypes.byref(b), ctypes.byref(o), _ptr(g), _ptr(order), _ptr(out.a), _ptr(out.dqfrc),
+        _ptr(out.daref), _ptr(out.dJ), _ptr(out.status), _ptr(out.iters), _ptr(out.workspace),
+        out.workspace.numel(), _stream()), "cs_solve_fused_ncg")
+    return out
+
+
 @dataclasses.dataclass
 class EllipticOut:
     """Outputs of the round-cone fused solve (packed like the batch)."""
