@@ -405,6 +405,8 @@ def run_gpu(args):
         line["adjoint_memory"] = run_memory(args)
     if not args.no_elliptic and world == 1:
         line["elliptic"] = run_elliptic(args)
+    if not args.no_ncg and world == 1:
+        line["ncg"] = run_ncg(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, max_instances=args.cpu_sample)
     print(json.dumps(line), flush=True)
@@ -555,6 +557,44 @@ def run_elliptic(args):
     return res
 
 
+def run_ncg(args):
+    """The headline batch solved by nonlinear conjugate gradients (the other
+    forward solver of Section III-B) feeding the same IFT adjoint: one fused
+    launch per step, CUDA-event timed."""
+    import torch
+    from paper_2607_24959_b300 import solver, workloads as W
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    w = W.quadruped()
+    batch = solver.DeviceBatch.from_workload(w, dev)
+    g = torch.from_numpy(w.g).to(dev)
+    order = torch.from_numpy(solver.cost_order(w.inst)).to(dev)
+    out = solver.solve_fused_ncg(batch, g, order=order, tol=args.tol)
+    stream = torch.cuda.Stream(device=dev)
+    steps = 3
+    with torch.cuda.stream(stream):
+        solver.solve_fused_ncg(batch, g, order=order, tol=args.tol, out=out)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            solver.solve_fused_ncg(batch, g, order=order, tol=args.tol, out=out)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = out.status.cpu().numpy()[:w.n]
+    it = out.iters.cpu().numpy()[:w.n]
+    res = {"metric": "fwd+IFT-adjoint solves/s with the conjugate-gradient forward solver",
+           "value": w.n / (ms / 1e3), "unit": "solves/s", "ms_per_step": ms, "steps": steps,
+           "config": {"workload": "quadruped", "instances": w.n,
+                      "max_iter": solver.NCG_MAX_ITER},
+           "status_counts": np.bincount(st, minlength=6).tolist(),
+           "iters_mean": float(it.mean()), "iters_max": int(it.max())}
+    del out, batch
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_e2e(args, w, batch, dev, kw, world):
     """Same metric through the public API with pinned host buffers: every step
     copies its inputs host->device and its results device->host
@@ -600,6 +640,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=32768)
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-ncg", action="store_true",
+                    help="skip the conjugate-gradient forward solver leg")
     ap.add_argument("--no-elliptic", action="store_true",
                     help="skip the round-cone throughput leg")
     ap.add_argument("--no-memory", action="store_true",
