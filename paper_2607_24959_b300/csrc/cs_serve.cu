@@ -46,11 +46,53 @@ double now_s() {
 inline size_t al4(size_t n) { return (n + 3) & ~(size_t)3; }
 inline size_t al256(size_t n) { return (n + 255) & ~(size_t)255; }
 
+// Host buffer of a request (uninitialised floats; capacity a power of two).
+struct Buf {
+  std::unique_ptr<float[]> p;
+  size_t cap = 0;
+  float* data() { return p.get(); }
+  const float* data() const { return p.get(); }
+};
+
+// Recycles request buffers by power-of-two size class: a fresh allocation per
+// request (page faults on large mappings, zero-filling) made submission the
+// bottleneck of a high-rate client.
+struct BufPool {
+  std::mutex mu;
+  std::vector<Buf> free_[40];
+  static int cls(size_t n) {
+    int c = 0;
+    while (((size_t)1 << c) < n) ++c;
+    return c;
+  }
+  Buf get(size_t n) {
+    const int c = cls(n ? n : 1);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!free_[c].empty()) {
+        Buf b = std::move(free_[c].back());
+        free_[c].pop_back();
+        return b;
+      }
+    }
+    Buf b;
+    b.cap = (size_t)1 << c;
+    b.p.reset(new float[b.cap]);
+    return b;
+  }
+  void put(Buf&& b) {
+    if (!b.p) return;
+    const int c = cls(b.cap);
+    std::lock_guard<std::mutex> lk(mu);
+    if (free_[c].size() < 4096) free_[c].push_back(std::move(b));
+  }
+};
+
 struct Req {
   uint64_t ticket = 0;
   int nv = 0, m = 0;
-  std::vector<float> in;   // M, J, qfrc, aref, D, g (packed back to back)
-  std::vector<float> out;  // a, dqfrc, daref, dJ
+  Buf in;   // M, J, qfrc, aref, D, g (packed back to back)
+  Buf out;  // a, dqfrc, daref, dJ
   int32_t status = 0, iters = 0;
   double t_submit = 0, t_start = 0, t_done = 0;
   std::atomic<int> state{0};  // 0 queued, 1 on the GPU, 2 done
@@ -90,6 +132,7 @@ struct cs_server {
   std::condition_variable cv;
   std::deque<std::shared_ptr<cs::Req>> queue;
   std::unordered_map<uint64_t, std::shared_ptr<cs::Req>> tickets;
+  cs::BufPool pool;  // request buffers, returned when a ticket is retired
   uint64_t next_ticket = 1;
   bool stop = false;
   bool flush = false;
@@ -436,7 +479,7 @@ int cs_serve_submit(cs_server* S, const cs_request* q, uint64_t* ticket) {
   r->nv = q->nv;
   r->m = q->m;
   const size_t nn = (size_t)q->nv * q->nv, mn = (size_t)q->m * q->nv;
-  r->in.resize(nn + mn + 2 * (size_t)q->nv + 2 * (size_t)q->m);
+  r->in = S->pool.get(nn + mn + 2 * (size_t)q->nv + 2 * (size_t)q->m);
   float* d = r->in.data();
   memcpy(d, q->M, nn * 4);
   d += nn;
@@ -449,7 +492,7 @@ int cs_serve_submit(cs_server* S, const cs_request* q, uint64_t* ticket) {
   if (q->m) memcpy(d, q->D, q->m * 4);
   d += q->m;
   memcpy(d, q->g, q->nv * 4);
-  r->out.resize(2 * (size_t)q->nv + q->m + mn);
+  r->out = S->pool.get(2 * (size_t)q->nv + q->m + mn);
   r->t_submit = now_s();
   {
     std::lock_guard<std::mutex> lk(S->mu);
@@ -465,6 +508,22 @@ int cs_serve_submit(cs_server* S, const cs_request* q, uint64_t* ticket) {
   return CS_OK;
 }
 
+namespace {
+// Copy a finished request's outputs and times into res (outside the lock).
+void fill_result(const Req* r, cs_result* res) {
+  const float* o = r->out.data();
+  if (res->a) memcpy(res->a, o, r->nv * 4);
+  if (res->dqfrc) memcpy(res->dqfrc, o + r->nv, r->nv * 4);
+  if (res->daref && r->m) memcpy(res->daref, o + 2 * r->nv, r->m * 4);
+  if (res->dJ && r->m) memcpy(res->dJ, o + 2 * r->nv + r->m, (size_t)r->m * r->nv * 4);
+  res->status = r->status;
+  res->iters = r->iters;
+  res->t_submit = r->t_submit;
+  res->t_start = r->t_start;
+  res->t_done = r->t_done;
+}
+}  // namespace
+
 int cs_serve_poll(cs_server* S, uint64_t ticket, cs_result* res) {
   if (!S || !res) return set_error(CS_EINVAL, "server and result must not be NULL");
   std::shared_ptr<Req> r;
@@ -476,16 +535,9 @@ int cs_serve_poll(cs_server* S, uint64_t ticket, cs_result* res) {
     if (r->state.load(std::memory_order_acquire) != 2) return CS_PENDING;
     S->tickets.erase(it);
   }
-  const float* o = r->out.data();
-  if (res->a) memcpy(res->a, o, r->nv * 4);
-  if (res->dqfrc) memcpy(res->dqfrc, o + r->nv, r->nv * 4);
-  if (res->daref && r->m) memcpy(res->daref, o + 2 * r->nv, r->m * 4);
-  if (res->dJ && r->m) memcpy(res->dJ, o + 2 * r->nv + r->m, (size_t)r->m * r->nv * 4);
-  res->status = r->status;
-  res->iters = r->iters;
-  res->t_submit = r->t_submit;
-  res->t_start = r->t_start;
-  res->t_done = r->t_done;
+  fill_result(r.get(), res);
+  S->pool.put(std::move(r->in));
+  S->pool.put(std::move(r->out));
   return CS_OK;
 }
 
@@ -503,14 +555,33 @@ int cs_serve_poll_batch(cs_server* S, int32_t n, const uint64_t* tickets, cs_res
                         int32_t* done) {
   if (!S || n < 0 || (n > 0 && (!tickets || !res || !done)))
     return set_error(CS_EINVAL, "server, tickets, results and done must not be NULL");
-  int count = 0;
-  for (int32_t i = 0; i < n; ++i) {
-    if (done[i] == 1) continue;  // collected by an earlier call
-    const int rc = cs_serve_poll(S, tickets[i], res + i);
-    done[i] = rc == CS_OK ? 1 : (rc == CS_PENDING ? 0 : -1);
-    count += rc == CS_OK;
+  // one pass under the lock (a poller holding many tickets must not contend
+  // with the scheduler once per ticket), outputs copied after it
+  std::vector<std::pair<int32_t, std::shared_ptr<Req>>> ready;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (int32_t i = 0; i < n; ++i) {
+      if (done[i] == 1) continue;  // collected by an earlier call
+      auto it = S->tickets.find(tickets[i]);
+      if (it == S->tickets.end()) {
+        done[i] = -1;
+        continue;
+      }
+      if (it->second->state.load(std::memory_order_acquire) != 2) {
+        done[i] = 0;
+        continue;
+      }
+      ready.emplace_back(i, it->second);
+      S->tickets.erase(it);
+    }
   }
-  return count;
+  for (auto& pr : ready) {
+    fill_result(pr.second.get(), res + pr.first);
+    S->pool.put(std::move(pr.second->in));
+    S->pool.put(std::move(pr.second->out));
+    done[pr.first] = 1;
+  }
+  return (int)ready.size();
 }
 
 int cs_serve_cancel(cs_server* S, uint64_t ticket) {
