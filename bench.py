@@ -663,7 +663,7 @@ def main():
                     help="skip the round-cone throughput leg")
     ap.add_argument("--no-memory", action="store_true",
                     help="skip the IFT vs unrolled differentiation memory sweeps")
-    ap.add_argument("--e2e-chunks", type=int, default=8)
+    ap.add_argument("--e2e-chunks", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-rate", type=float, default=50000.0)
     ap.add_argument("--serve-fixed-batch", type=int, default=1024)
