@@ -300,16 +300,18 @@ struct WarpSolver {
   // z = (L L^T)^-1 x, vectors spread one element per lane.
   __device__ __forceinline__ float chol_solve(float x) {
     const float* L = Ls();
-    const float* dv = Vec(V_DINV);
+    // each lane's own reciprocal pivot, read once: a shared-memory load per
+    // step would sit on the solve's dependency chain
+    const float dme = Vec(V_DINV)[min(lane, NV - 1)];
 #pragma unroll 1
     for (int k = 0; k < NV; ++k) {
-      if (lane == k) x *= dv[k];
+      if (lane == k) x *= dme;
       const float yk = __shfl_sync(kFull, x, k);
       if (lane > k && lane < NV) x = __fmaf_rn(-L[lane * G::MS + k], yk, x);
     }
 #pragma unroll 1
     for (int k = NV - 1; k >= 0; --k) {
-      if (lane == k) x *= dv[k];
+      if (lane == k) x *= dme;
       const float zk = __shfl_sync(kFull, x, k);
       if (lane < k) x = __fmaf_rn(-L[k * G::MS + lane], zk, x);
     }
