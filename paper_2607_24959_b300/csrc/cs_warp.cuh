@@ -12,7 +12,8 @@
 //    accumulated with error-free transformations (TwoSum / TwoProd), so the
 //    contact forces f keep their accuracy when a stiff row has |jar| << |J a|;
 //  * H = M + sum_{i active} D_i J_i^T J_i (Eq. 9), a left-looking Cholesky in
-//    shared memory (lane j computes row j), triangular solves by shuffles;
+//    shared memory (lane j computes row j), blocked triangular solves with
+//    shuffles;
 //  * p = -H^-1 r and an exact line search on the piecewise-linear derivative
 //    of phi(alpha) = L(a + alpha p) (Eq. 10): safeguarded Newton on phi' that
 //    stops when no breakpoint separates the trial point from its Newton
@@ -298,22 +299,59 @@ struct WarpSolver {
   }
 
   // z = (L L^T)^-1 x, vectors spread one element per lane.
+  //
+  // Blocked substitution: per block of kSB unknowns, the partially reduced
+  // right-hand sides are gathered from their lanes with independent
+  // shuffles, every lane solves the kSB x kSB diagonal block itself (L and
+  // the reciprocal pivots are shared-memory broadcasts), and each lane below
+  // (forward) or above (backward) the block subtracts the block's part.
+  // Every unknown sees the same fused multiply-adds in the same order as in
+  // column-at-a-time substitution, so the result is identical bit for bit;
+  // the dependency chain has one shuffle per block instead of per column.
+  static constexpr int kSB = (NV % 4 == 0) ? 4 : (NV % 3 == 0) ? 3 : (NV % 2 == 0) ? 2 : 1;
   __device__ __forceinline__ float chol_solve(float x) {
     const float* L = Ls();
-    // each lane's own reciprocal pivot, read once: a shared-memory load per
-    // step would sit on the solve's dependency chain
-    const float dme = Vec(V_DINV)[min(lane, NV - 1)];
+    const float* dinv = Vec(V_DINV);
+    const float* Lrow = L + min(lane, NV - 1) * G::MS;
 #pragma unroll 1
-    for (int k = 0; k < NV; ++k) {
-      if (lane == k) x *= dme;
-      const float yk = __shfl_sync(kFull, x, k);
-      if (lane > k && lane < NV) x = __fmaf_rn(-L[lane * G::MS + k], yk, x);
+    for (int kb = 0; kb < NV; kb += kSB) {
+      float y[kSB];
+#pragma unroll
+      for (int u = 0; u < kSB; ++u) y[u] = __shfl_sync(kFull, x, kb + u);
+#pragma unroll
+      for (int u = 0; u < kSB; ++u) {
+        const float* Lu = L + (kb + u) * G::MS + kb;
+#pragma unroll
+        for (int w = 0; w < u; ++w) y[u] = __fmaf_rn(-Lu[w], y[w], y[u]);
+        y[u] *= dinv[kb + u];
+      }
+      if (lane >= kb + kSB && lane < NV) {
+#pragma unroll
+        for (int u = 0; u < kSB; ++u) x = __fmaf_rn(-Lrow[kb + u], y[u], x);
+      }
+#pragma unroll
+      for (int u = 0; u < kSB; ++u)
+        if (lane == kb + u) x = y[u];
     }
 #pragma unroll 1
-    for (int k = NV - 1; k >= 0; --k) {
-      if (lane == k) x *= dme;
-      const float zk = __shfl_sync(kFull, x, k);
-      if (lane < k) x = __fmaf_rn(-L[k * G::MS + lane], zk, x);
+    for (int kt = NV - kSB; kt >= 0; kt -= kSB) {
+      float z[kSB];
+#pragma unroll
+      for (int u = 0; u < kSB; ++u) z[u] = __shfl_sync(kFull, x, kt + u);
+#pragma unroll
+      for (int u = kSB - 1; u >= 0; --u) {
+#pragma unroll
+        for (int w = kSB - 1; w > u; --w)
+          z[u] = __fmaf_rn(-L[(kt + w) * G::MS + kt + u], z[w], z[u]);
+        z[u] *= dinv[kt + u];
+      }
+      if (lane < kt) {
+#pragma unroll
+        for (int w = kSB - 1; w >= 0; --w) x = __fmaf_rn(-L[(kt + w) * G::MS + lane], z[w], x);
+      }
+#pragma unroll
+      for (int u = 0; u < kSB; ++u)
+        if (lane == kt + u) x = z[u];
     }
     return (lane < NV) ? x : 0.f;
   }
