@@ -263,35 +263,78 @@ struct WarpSolver {
   // reciprocal pivots go to the V_DINV slot.  Returns false on a non-positive
   // pivot.  The fp32 factor is only the preconditioner of a compensated
   // iteration, so the reciprocal square root is the MUFU one.
+  //
+  // Blocked by kSB columns: each lane forms its row's kSB partial dot
+  // products against the finished columns in one pass (kSB independent
+  // chains), the kSB x kSB diagonal block is gathered by shuffles and
+  // factored by every lane, and each lane finishes its own row of the block
+  // column; one warp barrier per block instead of two per column.
   __device__ __forceinline__ bool factor() {
     float* L = Ls();
     float* dv = Vec(V_DINV);
-    const float* Lj = L + min(lane, NV - 1) * G::MS;
+    float* Lj = L + min(lane, NV - 1) * G::MS;
     bool ok = true;
 #pragma unroll 1
-    for (int k = 0; k < NV; ++k) {
-      const float* Lk = L + k * G::MS;
-      float acc = Lj[k], acc2 = 0.f;
-      int i = 0;
+    for (int kb = 0; kb < NV; kb += kSB) {
+      const float* Lb = L + kb * G::MS;
+      // H[j][kb+u] - sum_{i<kb} L[j][i] L[kb+u][i] (lanes j < kb+u read
+      // entries above the diagonal: their values are never used)
+      float acc[kSB];
+#pragma unroll
+      for (int u = 0; u < kSB; ++u) acc[u] = Lj[kb + u];
 #pragma unroll 1
-      for (; i + 1 < k; i += 2) {
-        acc = __fmaf_rn(-Lj[i], Lk[i], acc);
-        acc2 = __fmaf_rn(-Lj[i + 1], Lk[i + 1], acc2);
+      for (int i = 0; i < kb; ++i) {
+        const float x = Lj[i];
+#pragma unroll
+        for (int u = 0; u < kSB; ++u) acc[u] = __fmaf_rn(-x, Lb[u * G::MS + i], acc[u]);
       }
-      if (i < k) acc = __fmaf_rn(-Lj[i], Lk[i], acc);
-      acc += acc2;
-      const float d = __shfl_sync(kFull, acc, k);
-      ok = ok && (d > 0.f) && (d < CUDART_INF_F);
-      const float rs = rsqrtf(d);
+      // the diagonal block, row kb+u of it from lane kb+u
+      float blk[kSB][kSB];
+#pragma unroll
+      for (int u = 0; u < kSB; ++u)
+#pragma unroll
+        for (int w = 0; w <= u; ++w) blk[u][w] = __shfl_sync(kFull, acc[w], kb + u);
+      float rs[kSB], lkk[kSB];
+#pragma unroll
+      for (int w = 0; w < kSB; ++w) {
+        float d = blk[w][w];
+#pragma unroll
+        for (int v = 0; v < w; ++v) d = __fmaf_rn(-blk[w][v], blk[w][v], d);
+        ok = ok && (d > 0.f) && (d < CUDART_INF_F);
+        rs[w] = rsqrtf(d);
+        lkk[w] = d * rs[w];
+#pragma unroll
+        for (int u = w + 1; u < kSB; ++u) {
+          float e = blk[u][w];
+#pragma unroll
+          for (int v = 0; v < w; ++v) e = __fmaf_rn(-blk[u][v], blk[w][v], e);
+          blk[u][w] = e * rs[w];
+        }
+        blk[w][w] = lkk[w];
+      }
+      // this lane's row of the block column
+      float out[kSB];
+#pragma unroll
+      for (int w = 0; w < kSB; ++w) {
+        float e = acc[w];
+#pragma unroll
+        for (int v = 0; v < w; ++v) e = __fmaf_rn(-out[v], blk[w][v], e);
+        out[w] = e * rs[w];
+      }
       __syncwarp();
-      if (lane == k) {
-        // the reciprocal pivot is derived from the stored diagonal, exactly as
-        // load_factor() does, so a kept factor solves bit-identically
-        const float lkk = d * rs;
-        L[k * G::MS + k] = lkk;
-        dv[k] = 1.0f / lkk;
-      } else if (lane > k && lane < NV) {
-        L[lane * G::MS + k] = acc * rs;
+      if (lane >= kb + kSB && lane < NV) {
+#pragma unroll
+        for (int w = 0; w < kSB; ++w) Lj[kb + w] = out[w];
+      }
+#pragma unroll
+      for (int u = 0; u < kSB; ++u) {
+        if (lane == kb + u) {
+#pragma unroll
+          for (int w = 0; w <= u; ++w) Lj[kb + w] = blk[u][w];
+          // the reciprocal pivot is derived from the stored diagonal, exactly
+          // as load_factor() does, so a kept factor solves bit-identically
+          dv[kb + u] = 1.0f / lkk[u];
+        }
       }
       __syncwarp();
     }
