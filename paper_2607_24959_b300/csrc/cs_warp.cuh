@@ -264,9 +264,9 @@ struct WarpSolver {
   // pivot.  The fp32 factor is only the preconditioner of a compensated
   // iteration, so the reciprocal square root is the MUFU one.
   //
-  // Blocked by kSB columns: each lane forms its row's kSB partial dot
-  // products against the finished columns in one pass (kSB independent
-  // chains), the kSB x kSB diagonal block is gathered by shuffles and
+  // Blocked by kFB columns: each lane forms its row's kFB partial dot
+  // products against the finished columns in one pass (kFB independent
+  // chains), the kFB x kFB diagonal block is gathered by shuffles and
   // factored by every lane, and each lane finishes its own row of the block
   // column; one warp barrier per block instead of two per column.
   __device__ __forceinline__ bool factor() {
@@ -275,28 +275,28 @@ struct WarpSolver {
     float* Lj = L + min(lane, NV - 1) * G::MS;
     bool ok = true;
 #pragma unroll 1
-    for (int kb = 0; kb < NV; kb += kSB) {
+    for (int kb = 0; kb < NV; kb += kFB) {
       const float* Lb = L + kb * G::MS;
       // H[j][kb+u] - sum_{i<kb} L[j][i] L[kb+u][i] (lanes j < kb+u read
       // entries above the diagonal: their values are never used)
-      float acc[kSB];
+      float acc[kFB];
 #pragma unroll
-      for (int u = 0; u < kSB; ++u) acc[u] = Lj[kb + u];
+      for (int u = 0; u < kFB; ++u) acc[u] = Lj[kb + u];
 #pragma unroll 1
       for (int i = 0; i < kb; ++i) {
         const float x = Lj[i];
 #pragma unroll
-        for (int u = 0; u < kSB; ++u) acc[u] = __fmaf_rn(-x, Lb[u * G::MS + i], acc[u]);
+        for (int u = 0; u < kFB; ++u) acc[u] = __fmaf_rn(-x, Lb[u * G::MS + i], acc[u]);
       }
       // the diagonal block, row kb+u of it from lane kb+u
-      float blk[kSB][kSB];
+      float blk[kFB][kFB];
 #pragma unroll
-      for (int u = 0; u < kSB; ++u)
+      for (int u = 0; u < kFB; ++u)
 #pragma unroll
         for (int w = 0; w <= u; ++w) blk[u][w] = __shfl_sync(kFull, acc[w], kb + u);
-      float rs[kSB], lkk[kSB];
+      float rs[kFB], lkk[kFB];
 #pragma unroll
-      for (int w = 0; w < kSB; ++w) {
+      for (int w = 0; w < kFB; ++w) {
         float d = blk[w][w];
 #pragma unroll
         for (int v = 0; v < w; ++v) d = __fmaf_rn(-blk[w][v], blk[w][v], d);
@@ -304,7 +304,7 @@ struct WarpSolver {
         rs[w] = rsqrtf(d);
         lkk[w] = d * rs[w];
 #pragma unroll
-        for (int u = w + 1; u < kSB; ++u) {
+        for (int u = w + 1; u < kFB; ++u) {
           float e = blk[u][w];
 #pragma unroll
           for (int v = 0; v < w; ++v) e = __fmaf_rn(-blk[u][v], blk[w][v], e);
@@ -313,21 +313,21 @@ struct WarpSolver {
         blk[w][w] = lkk[w];
       }
       // this lane's row of the block column
-      float out[kSB];
+      float out[kFB];
 #pragma unroll
-      for (int w = 0; w < kSB; ++w) {
+      for (int w = 0; w < kFB; ++w) {
         float e = acc[w];
 #pragma unroll
         for (int v = 0; v < w; ++v) e = __fmaf_rn(-out[v], blk[w][v], e);
         out[w] = e * rs[w];
       }
       __syncwarp();
-      if (lane >= kb + kSB && lane < NV) {
+      if (lane >= kb + kFB && lane < NV) {
 #pragma unroll
-        for (int w = 0; w < kSB; ++w) Lj[kb + w] = out[w];
+        for (int w = 0; w < kFB; ++w) Lj[kb + w] = out[w];
       }
 #pragma unroll
-      for (int u = 0; u < kSB; ++u) {
+      for (int u = 0; u < kFB; ++u) {
         if (lane == kb + u) {
 #pragma unroll
           for (int w = 0; w <= u; ++w) Lj[kb + w] = blk[u][w];
@@ -352,6 +352,7 @@ struct WarpSolver {
   // column-at-a-time substitution, so the result is identical bit for bit;
   // the dependency chain has one shuffle per block instead of per column.
   static constexpr int kSB = (NV % 4 == 0) ? 4 : (NV % 3 == 0) ? 3 : (NV % 2 == 0) ? 2 : 1;
+  static constexpr int kFB = kSB;  // Cholesky block edge
   __device__ __forceinline__ float chol_solve(float x) {
     const float* L = Ls();
     const float* dinv = Vec(V_DINV);
