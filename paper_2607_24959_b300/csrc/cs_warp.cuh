@@ -401,10 +401,13 @@ struct WarpSolver {
 #pragma unroll
       for (int u = 0; u < kFB; ++u) acc[u] = Lj[kb + u];
 #pragma unroll 1
-      for (int i = 0; i < kb; ++i) {
-        const float x = Lj[i];
+      for (int i = 0; i < kb; i += kFB) {
 #pragma unroll
-        for (int u = 0; u < kFB; ++u) acc[u] = __fmaf_rn(-x, Lb[u * G::MS + i], acc[u]);
+        for (int v = 0; v < kFB; ++v) {
+          const float x = Lj[i + v];
+#pragma unroll
+          for (int u = 0; u < kFB; ++u) acc[u] = __fmaf_rn(-x, Lb[u * G::MS + i + v], acc[u]);
+        }
       }
       // the diagonal block, row kb+u of it from lane kb+u
       float blk[kFB][kFB];
@@ -612,7 +615,7 @@ struct WarpSolver {
     const float* Jm = Js() + lane * G::JS;
 #pragma unroll
     for (int t = 0; t < MT; ++t) { s[t] = 0.f; c[t] = 0.f; }
-#pragma unroll 1
+#pragma unroll (kSB)
     for (int k = 0; k < NV; ++k) {
       const float xh = vh[k], xl = vl[k];
 #pragma unroll
@@ -660,7 +663,7 @@ struct WarpSolver {
     c = 0.f;
     if (lane < NV) {
       const float* Mr = Ms() + lane * G::MS;
-#pragma unroll 1
+#pragma unroll (kSB)
       for (int k = 0; k < NV; ++k) dot2(s, c, Mr[k], vh[k], vl[k]);
     }
   }
@@ -670,7 +673,7 @@ struct WarpSolver {
     const float* Jm = Js() + lane * G::JS;
 #pragma unroll
     for (int t = 0; t < MT; ++t) s[t] = 0.f;
-#pragma unroll 1
+#pragma unroll (kSB)
     for (int k = 0; k < NV; ++k) {
       const float xh = vh[k];
 #pragma unroll
@@ -698,7 +701,7 @@ struct WarpSolver {
     float s = 0.f;
     if (lane < NV) {
       const float* Mr = Ms() + lane * G::MS;
-#pragma unroll 1
+#pragma unroll (kSB)
       for (int k = 0; k < NV; ++k) s = __fmaf_rn(Mr[k], vh[k], s);
     }
     return s;
@@ -809,7 +812,7 @@ struct WarpSolver {
     for (int t = 0; t < MT; ++t) s_r[t] = 0.f;
     float Mp = 0.f;
     const float* Mr = Ms() + min(lane, NV - 1) * G::MS;
-#pragma unroll 1
+#pragma unroll (kSB)
     for (int k = 0; k < NV; ++k) {
       const float pk = vp[k];
 #pragma unroll
