@@ -126,6 +126,16 @@ def algorithmic_work(inst, iters, act_counts):
     return float(flops.sum()), float(byts.sum())
 
 
+# DRAM bytes (read + write) of one step of the fused warp kernels on the
+# 32768-instance quadruped batch: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of the four bucket kernels captured on 8192 instances
+# (59.34 MB), scaled by instances.  Must be re-taken whenever the kernel changes.
+QUADRUPED_STEP_TRAFFIC = (
+    32768, 4 * 59.341312e6,
+    "ncu capture of the current warp kernel on 8192 quadruped instances, scaled x4 "
+    "(profiles/warp_solve_fused_quadruped_ncu.md)")
+
+
 def make_workload(name, rank, n=None):
     from paper_2607_24959_b300 import workloads as W
     seed_shift = 7919 * rank
@@ -387,6 +397,9 @@ def run_gpu(args):
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": frac_hbm, "traffic": None}
+    if args.workload == "quadruped" and w.n == QUADRUPED_STEP_TRAFFIC[0]:
+        roof["traffic"] = QUADRUPED_STEP_TRAFFIC[1]
+        roof["traffic_source"] = QUADRUPED_STEP_TRAFFIC[2]
     roof["kernel"] = "warp_solve_kernel<NV,MT,FUSED> buckets (all launches of one step)"
     roof["algorithmic_flops_per_launch"] = flops
     roof["algorithmic_bytes_per_launch"] = byts
@@ -664,7 +677,7 @@ def main():
     ap.add_argument("--no-memory", action="store_true",
                     help="skip the IFT vs unrolled differentiation memory sweeps")
     ap.add_argument("--e2e-chunks", type=int, default=4)
-    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-requests", type=int, default=200000)
     ap.add_argument("--serve-rate", type=float, default=50000.0)
     ap.add_argument("--serve-fixed-batch", type=int, default=1024)
     args = ap.parse_args()
