@@ -10,7 +10,7 @@ namespace cs {
 template <int NV, int MT, int MODE>
 static cudaError_t launch_t(const csk::Params& P, const LaunchCfg& cfg, cudaStream_t s,
                             KernelInfo* info) {
-  using G = csk::Geo<NV, MT>;
+  using G = csk::Geo<NV, MT, true>;  // the layout warp_solve_kernel uses
   auto kern = csk::warp_solve_kernel<NV, MT, MODE>;
   int wpb = cfg.warps_per_block > 0 ? cfg.warps_per_block : 4;
   if (wpb > 8) wpb = 8;

@@ -90,7 +90,13 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 // ------------------------------------------------------------------ geometry
-template <int NV, int MT>
+// kShare: lambda and its low part reuse the words of D and of f's low part,
+// which are dead while the adjoint runs (D in shared memory is read only by
+// the assembly, which precedes the adjoint; f's low part only by the
+// compensated residual; f itself stays, the gradient writer reads it).  The
+// warp kernel's own modes use it; callers that keep f, its low part and
+// lambda live together (the unrolled reverse sweep, the round cone) do not.
+template <int NV, int MT, bool kShare = false>
 struct Geo {
   static_assert(NV >= 1 && NV <= 32, "one lane per row of H");
   static constexpr int MCAP = 32 * MT;               // rows per instance
@@ -106,9 +112,9 @@ struct Geo {
   static constexpr int oJ = oL + NV * MS;            // J   MCAP x JS
   static constexpr int oD = oJ + MCAP * JS;          // D   MCAP
   static constexpr int oF = oD + MCAP;               // f   MCAP
-  static constexpr int oLam = oF + MCAP;             // lambda = D_act J w
-  static constexpr int oFlo = oLam + MCAP;           // low parts of f ...
-  static constexpr int oLamlo = oFlo + MCAP;         // ... and of lambda
+  static constexpr int oLam = kShare ? oD : oF + MCAP;              // lambda = D_act J w
+  static constexpr int oFlo = kShare ? oF + MCAP : oLam + MCAP;     // low parts of f ...
+  static constexpr int oLamlo = kShare ? oFlo : oFlo + MCAP;        // ... and of lambda
   static constexpr int oIdx = oLamlo + MCAP;         // active rows (int)
   static constexpr int oVec = oIdx + MCAP;           // broadcast vectors
   static constexpr int kVec = 7;
@@ -141,9 +147,9 @@ struct Params {
 
 enum Mode { MODE_FWD = 0, MODE_ADJ = 1, MODE_FUSED = 2, MODE_FUSED_NCG = 3 };
 
-template <int NV, int MT>
+template <int NV, int MT, bool kShare = false>
 struct WarpSolver {
-  using G = Geo<NV, MT>;
+  using G = Geo<NV, MT, kShare>;
   float* sm;   // warp slice
   int lane;
 
@@ -1287,9 +1293,9 @@ struct WarpSolver {
 template <int NV, int MT, int MODE>
 __global__ void __launch_bounds__(256) warp_solve_kernel(const __grid_constant__ Params P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  using G = Geo<NV, MT>;
+  using G = Geo<NV, MT, true>;
   const int warp = threadIdx.x >> 5;
-  WarpSolver<NV, MT> S;
+  WarpSolver<NV, MT, true> S;
   S.sm = reinterpret_cast<float*>(smem_raw + (size_t)warp * G::kBytes);
   S.lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
