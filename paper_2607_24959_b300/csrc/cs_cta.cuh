@@ -188,7 +188,10 @@ struct CtaSolver {
   // ------------------------------------------------------------- Cholesky
   // Blocked right-looking Cholesky, in place on the lower rows of Ls() (the
   // padded rows are identity), panels of 32 columns:
-  //  1. the diagonal block by warp 0, left-looking (lane l = row kb + l);
+  //  1. the diagonal block by warp 0, left-looking (lane l = row kb + l),
+  //     four columns per round: each lane forms its row's four partial dot
+  //     products in one pass, the 4 x 4 diagonal block is gathered by
+  //     shuffles and factored by every lane, one warp barrier pair per round;
   //  2. the rows below it by forward substitution against that block, four
   //     threads per row splitting each inner product;
   //  3. the trailing matrix updated by all threads in 2x2 register blocks.
@@ -203,34 +206,65 @@ struct CtaSolver {
       const int bs = min(32, nc - kb);
       if (warp == 0) {
         const int row = kb + min(lane, bs - 1);
-        const float* Lr = L + row * MS + kb;
+        float* Lr = L + row * MS + kb;
 #pragma unroll 1
-        for (int k = 0; k < bs; ++k) {
-          const float* Lk = L + (kb + k) * MS + kb;
-          float a0 = Lr[k], a1 = 0.f, a2 = 0.f, a3 = 0.f;
-          int i = 0;
+        for (int cb = 0; cb < bs; cb += 4) {  // bs is a multiple of 4
+          const float* Lb = L + (kb + cb) * MS + kb;
+          float acc[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] = Lr[cb + u];
 #pragma unroll 1
-          for (; i + 3 < k; i += 4) {
-            const float x0 = Lr[i], x1 = Lr[i + 1], x2 = Lr[i + 2], x3 = Lr[i + 3];
-            const float y0 = Lk[i], y1 = Lk[i + 1], y2 = Lk[i + 2], y3 = Lk[i + 3];
-            a0 = __fmaf_rn(-x0, y0, a0);
-            a1 = __fmaf_rn(-x1, y1, a1);
-            a2 = __fmaf_rn(-x2, y2, a2);
-            a3 = __fmaf_rn(-x3, y3, a3);
+          for (int i = 0; i < cb; i += 4) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const float x = Lr[i + v];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) acc[u] = __fmaf_rn(-x, Lb[u * MS + i + v], acc[u]);
+            }
           }
-#pragma unroll 1
-          for (; i < k; ++i) a0 = __fmaf_rn(-Lr[i], Lk[i], a0);
-          const float acc = (a0 + a1) + (a2 + a3);
-          const float d = __shfl_sync(kFull, acc, k);
-          ok = ok && (d > 0.f) && (d < CUDART_INF_F);
-          const float rs = rsqrtf(d);
+          float blk[4][4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w <= u; ++w) blk[u][w] = __shfl_sync(kFull, acc[w], cb + u);
+          float rs[4], lkk[4];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            float d = blk[w][w];
+#pragma unroll
+            for (int v = 0; v < w; ++v) d = __fmaf_rn(-blk[w][v], blk[w][v], d);
+            ok = ok && (d > 0.f) && (d < CUDART_INF_F);
+            rs[w] = rsqrtf(d);
+            lkk[w] = d * rs[w];
+#pragma unroll
+            for (int u = w + 1; u < 4; ++u) {
+              float e = blk[u][w];
+#pragma unroll
+              for (int v = 0; v < w; ++v) e = __fmaf_rn(-blk[u][v], blk[w][v], e);
+              blk[u][w] = e * rs[w];
+            }
+            blk[w][w] = lkk[w];
+          }
+          float out[4];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            float e = acc[w];
+#pragma unroll
+            for (int v = 0; v < w; ++v) e = __fmaf_rn(-out[v], blk[w][v], e);
+            out[w] = e * rs[w];
+          }
           __syncwarp();
-          if (lane == k) {
-            const float lkk = d * rs;
-            L[(kb + k) * MS + kb + k] = lkk;
-            dv[kb + k] = 1.0f / lkk;
-          } else if (lane > k && lane < bs) {
-            L[row * MS + kb + k] = acc * rs;
+          if (lane >= cb + 4 && lane < bs) {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) Lr[cb + w] = out[w];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (lane == cb + u) {
+#pragma unroll
+              for (int w = 0; w <= u; ++w) Lr[cb + w] = blk[u][w];
+              dv[kb + cb + u] = 1.0f / lkk[u];
+            }
           }
           __syncwarp();
         }
@@ -313,13 +347,30 @@ struct CtaSolver {
     for (int kb = 0; kb < nc; kb += 32) {
       const int bs = min(32, nc - kb);
       if (warp == 0) {
+        // four unknowns per shuffle round, each lane solving the 4 x 4
+        // diagonal block itself (same operations in the same order as
+        // column-at-a-time substitution)
         float x = (lane < bs) ? X[kb + lane] : 0.f;
         const float* Lr = L + (kb + min(lane, bs - 1)) * MS + kb;
 #pragma unroll 1
-        for (int k = 0; k < bs; ++k) {
-          const float yk = __shfl_sync(kFull, x, k) * dv[kb + k];
-          const float upd = __fmaf_rn(-Lr[k], yk, x);
-          x = (lane == k) ? yk : ((lane > k && lane < bs) ? upd : x);
+        for (int cb = 0; cb < bs; cb += 4) {
+          float y[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) y[u] = __shfl_sync(kFull, x, cb + u);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float* Lu = L + (kb + cb + u) * MS + kb + cb;
+#pragma unroll
+            for (int w = 0; w < u; ++w) y[u] = __fmaf_rn(-Lu[w], y[w], y[u]);
+            y[u] = y[u] * dv[kb + cb + u];
+          }
+          if (lane >= cb + 4 && lane < bs) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x = __fmaf_rn(-Lr[cb + u], y[u], x);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (lane == cb + u) x = y[u];
         }
         if (lane < bs) X[kb + lane] = x;
       }
@@ -359,11 +410,25 @@ struct CtaSolver {
       if (warp == 0) {
         float x = (lane < bs) ? X[kb + lane] : 0.f;
 #pragma unroll 1
-        for (int k = bs - 1; k >= 0; --k) {
-          const float zk = __shfl_sync(kFull, x, k) * dv[kb + k];
-          const float lk = L[(kb + k) * MS + kb + min(lane, bs - 1)];
-          const float upd = __fmaf_rn(-lk, zk, x);
-          x = (lane == k) ? zk : ((lane < k) ? upd : x);
+        for (int ct = bs - 4; ct >= 0; ct -= 4) {
+          float z[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) z[u] = __shfl_sync(kFull, x, ct + u);
+#pragma unroll
+          for (int u = 3; u >= 0; --u) {
+#pragma unroll
+            for (int w = 3; w > u; --w)
+              z[u] = __fmaf_rn(-L[(kb + ct + w) * MS + kb + ct + u], z[w], z[u]);
+            z[u] = z[u] * dv[kb + ct + u];
+          }
+          if (lane < ct) {
+#pragma unroll
+            for (int w = 3; w >= 0; --w)
+              x = __fmaf_rn(-L[(kb + ct + w) * MS + kb + lane], z[w], x);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (lane == ct + u) x = z[u];
         }
         if (lane < bs) X[kb + lane] = x;
       }
