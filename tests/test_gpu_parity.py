@@ -167,6 +167,55 @@ def test_edge_cases(cuda_device):
         _check(w, parity.run_gpu_split(batch, w), np.arange(w.n), w.name + " split")
 
 
+def _pack_unaligned(parts, name):
+    """Pack instances back to back, with a one-float gap before every third
+    block, so that no block is 16-byte aligned by construction."""
+    nvs = [int(p["M"].shape[0]) for p in parts]
+    ms = [int(p["J"].size // nv) for p, nv in zip(parts, nvs)]
+    inst, _, _, _, _ = W.layout(nvs, ms)
+    arrays = {k: [] for k in ("M", "J", "qfrc", "aref", "D", "g")}
+    ends = {"M": 0, "J": 0, "v": 0, "r": 0}
+    for b, p in enumerate(parts):
+        gap = 1 if b % 3 == 1 else 0
+        for key, names in (("M", ("M",)), ("J", ("J",)), ("v", ("qfrc", "g")),
+                           ("r", ("aref", "D"))):
+            inst["off_" + key][b] = ends[key] + gap
+            for k in names:
+                arrays[k].append(np.zeros(gap, np.float32))
+                arrays[k].append(np.ravel(p[k]).astype(np.float32))
+            ends[key] += gap + np.ravel(p[names[0]]).size
+    cat = {k: np.concatenate(v) for k, v in arrays.items()}
+    return W.Workload(name, inst, cat["M"], cat["J"], cat["qfrc"], cat["aref"], cat["D"],
+                      cat["g"], {})
+
+
+def test_padded_instances_in_the_asynchronously_staged_kernels(cuda_device):
+    # nv below the kernel's NV (M padded with identity rows, J with zero
+    # columns, written by plain stores beside the asynchronous copies) in the
+    # kernels that stage by 4-byte cp.async (NV >= 16, or more than 64 rows),
+    # at every rows-per-lane count, packed with no block aligned
+    parts = []
+    for nv, nc, seed in ((13, 30, 21), (11, 24, 22), (17, 12, 23), (13, 8, 24), (25, 12, 25),
+                         (7, 20, 26)):
+        w = W.generate(f"pad{nv}", 20, nv, nc, seed=seed, cond=1e3)
+        parts += [w.instance(b) for b in range(w.n)]
+    rng = np.random.default_rng(27)
+    w = _pack_unaligned([parts[i] for i in rng.permutation(len(parts))], "padded-async")
+    assert np.any(w.inst["off_J"] % 4 != 0) and np.any(w.inst["off_M"] % 4 != 0)
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    _check(w, parity.run_gpu_fused(batch, w), np.arange(w.n), w.name)
+    _check(w, parity.run_gpu_split(batch, w), np.arange(w.n), w.name + " split")
+    g = torch.from_numpy(w.g).to(cuda_device)
+    plan = solver.FusedPlan(batch, g, autotune=False, graph=True)
+    out = plan.launch()
+    torch.cuda.synchronize()
+    got = dict(a=out.a.cpu().numpy(), dqfrc=out.dqfrc.cpu().numpy(),
+               daref=out.daref.cpu().numpy(), dJ=out.dJ.cpu().numpy(),
+               status=out.status.cpu().numpy(), iters=out.iters.cpu().numpy())
+    plan.close()
+    _check(w, got, np.arange(w.n), w.name + " plan")
+
+
 def test_max_rows_per_instance(cuda_device):
     w = W.generate("m256", 64, 18, 64, seed=13, cond=1e3)     # m = 256 rows
     batch = solver.DeviceBatch.from_workload(w, cuda_device)
