@@ -117,7 +117,7 @@ struct Geo {
   static constexpr int oLamlo = kShare ? oFlo : oFlo + MCAP;        // ... and of lambda
   static constexpr int oIdx = oLamlo + MCAP;         // active rows (int)
   static constexpr int oVec = oIdx + MCAP;           // broadcast vectors
-  static constexpr int kVec = 7;
+  static constexpr int kVec = kShare ? 4 : 7;        // broadcast slots (below)
   static constexpr int kWords = oVec + kVec * 32;
   static constexpr int kBytes = ((kWords * 4) + 127) & ~127;
 };
@@ -178,7 +178,15 @@ struct WarpSolver {
   __device__ __forceinline__ float* Flo() { return sm + G::oFlo; }
   __device__ __forceinline__ float* Lamlo() { return sm + G::oLamlo; }
   __device__ __forceinline__ int* Idx() { return reinterpret_cast<int*>(sm + G::oIdx); }
-  __device__ __forceinline__ float* Vec(int s) { return sm + G::oVec + 32 * s; }
+  // Broadcast slot of vector s.  kShare: w's pair takes the slots of p and of
+  // a's low part, and the gradient writer's copy of a the slot of a's high
+  // part (it holds the same value): in the warp kernel's modes the adjoint
+  // runs after the last line search and evaluates no residual.
+  __host__ __device__ static constexpr int slot(int s) {
+    return !kShare ? s
+                   : (s == V_WH ? V_P : s == V_WL ? V_AL : s == V_X ? V_AH : s == V_DINV ? 3 : s);
+  }
+  __device__ __forceinline__ float* Vec(int s) { return sm + G::oVec + 32 * slot(s); }
 
   __device__ __forceinline__ bool row_valid(int t) const { return lane + 32 * t < m; }
 
@@ -764,7 +772,7 @@ struct WarpSolver {
       }
     }
     nact = base;
-    fmax = warp_max(fm);
+    if (precise) fmax = warp_max(fm);  // read only by the compensated phase's step test
     __syncwarp();
     float js, jc, ms, mc;
     if (precise) {
@@ -790,7 +798,7 @@ struct WarpSolver {
       maq = 0.f;
     }
     const float rm = warp_max(fabsf(r));
-    const float sc = fmaxf(fmaxf(1.f, qmax), fmaxf(warp_max(fabsf(ms)), warp_max(fabsf(js))));
+    const float sc = fmaxf(fmaxf(1.f, qmax), warp_max(fmaxf(fabsf(ms), fabsf(js))));
     *scale = sc;
     *bad = __any_sync(kFull, !(fabsf(r) < CUDART_INF_F)) || !(sc < CUDART_INF_F);
     return rm;
