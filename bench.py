@@ -131,7 +131,7 @@ def algorithmic_work(inst, iters, act_counts):
 # dram__bytes_write.sum of the four bucket kernels captured on 8192 instances
 # (59.34 MB), scaled by instances.  Must be re-taken whenever the kernel changes.
 QUADRUPED_STEP_TRAFFIC = (
-    32768, 4 * 59.340288e6,
+    32768, 4 * 59.339776e6,
     "ncu capture of the current warp kernel on 8192 quadruped instances, scaled x4 "
     "(profiles/warp_solve_fused_quadruped_ncu.md)")
 
