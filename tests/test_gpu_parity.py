@@ -216,6 +216,33 @@ def test_padded_instances_in_the_asynchronously_staged_kernels(cuda_device):
     _check(w, got, np.arange(w.n), w.name + " plan")
 
 
+def test_cuda_path_matches_exact_golden_solutions(cuda_device):
+    # the stored exact minimisers and adjoints (exact rational arithmetic,
+    # tests/golden/make_golden.py), independent of the oracle
+    from tests.test_golden import load_cases
+    cases = load_cases()
+    parts = [dict(M=np.asarray(c["M"], np.float32),
+                  J=np.asarray(c["J"], np.float32).reshape(c["m"], c["nv"]),
+                  qfrc=np.asarray(c["qfrc"], np.float32), aref=np.asarray(c["aref"], np.float32),
+                  D=np.asarray(c["D"], np.float32), g=np.asarray(c["g"], np.float32))
+             for c in cases]
+    w = W.pack(parts, name="golden")
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    for label, got in (("fused", parity.run_gpu_fused(batch, w)),
+                       ("split", parity.run_gpu_split(batch, w))):
+        for b, c in enumerate(cases):
+            e = w.inst[b]
+            nv, m = int(e["nv"]), int(e["m"])
+            ov, orr, oJ = int(e["off_v"]), int(e["off_r"]), int(e["off_J"])
+            assert got["status"][b] == 0, (label, c["name"])
+            assert parity.rel(got["a"][ov:ov + nv], c["a"]) <= parity.A_TOL, (label, c["name"])
+            assert parity.rel(got["dqfrc"][ov:ov + nv], c["dqfrc"]) <= parity.G_TOL
+            dr = got["daref"][orr:orr + m]
+            assert parity.rel(dr, c["daref"]) <= parity.G_TOL, (label, c["name"])
+            assert ((dr != 0).astype(int).tolist() == c["active"]), (label, c["name"])
+            assert parity.rel(got["dJ"][oJ:oJ + m * nv], np.ravel(c["dJ"])) <= parity.G_TOL
+
+
 def test_max_rows_per_instance(cuda_device):
     w = W.generate("m256", 64, 18, 64, seed=13, cond=1e3)     # m = 256 rows
     batch = solver.DeviceBatch.from_workload(w, cuda_device)
