@@ -458,11 +458,11 @@ def run_memory(args):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
 
-    def measure(w, K):
+    def measure(w, K, methods=("ift", "unrolled")):
         batch = solver.DeviceBatch.from_workload(w, dev)
         g = torch.from_numpy(w.g).to(dev)
         res = {}
-        for name in ("ift", "unrolled"):
+        for name in methods:
             def once():
                 J = batch.J.clone().requires_grad_(True)
                 q = batch.qfrc.clone().requires_grad_(True)
@@ -542,6 +542,19 @@ def run_memory(args):
         "unrolled_peak": [r["unrolled"]["peak_bytes"] for r in rows],
         "unrolled_over_ift": [r["unrolled"]["peak_bytes"] / r["ift"]["peak_bytes"]
                               for r in rows]}
+    # the scaling extremes run one CTA per instance, beyond the unrolled
+    # path's one-warp sizes: the IFT adjoint's memory against the step cap
+    ext = {"config": "IFT adjoint through the autograd wrapper, step cap K; nv96: nv 96, "
+                     "16 contacts (64 rows), cond(M) 1e4, B 2048; nc256: nv 18, 256 contacts "
+                     "(1024 rows), B 256", "K": ks}
+    for label, w in (("nv96", W.nv96(seed=W.SEEDS["nv96"])),
+                     ("nc256", W.nc256(seed=W.SEEDS["nc256"] + 1))):
+        rows = [measure(w, K, ("ift",)) for K in ks]
+        peaks = [r["ift"]["peak_bytes"] for r in rows]
+        ext[label] = {"ift_peak": peaks, "ift_kept": [r["ift"]["kept_bytes"] for r in rows],
+                      "ift_ms": [r["ift"]["ms"] for r in rows],
+                      "ift_peak_change_K1_to_K10": peaks[-1] / peaks[0] - 1.0}
+    out["scaling_extremes"] = ext
     return out
 
 

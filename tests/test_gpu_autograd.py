@@ -50,3 +50,24 @@ def test_adjoint_memory_flat_in_iterations(cuda_device, keep_factor):
         del a, J
     assert len(set(state_bytes)) == 1
     assert max(peaks) == min(peaks), peaks
+
+
+@pytest.mark.parametrize("make", [lambda: W.nv96(n=256, seed=23), lambda: W.nc256(n=64, seed=24)],
+                         ids=["nv96", "nc256"])
+def test_adjoint_memory_flat_in_iterations_cta_sizes(cuda_device, make):
+    # the one-CTA-per-instance kernels (nv 96; 1024 rows): the same flat state
+    w = make()
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    g = torch.from_numpy(w.g).to(cuda_device)
+    peaks = []
+    for K in range(1, 11):
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        J = batch.J.clone().requires_grad_(True)
+        a = csag.contact_solve(batch, J=J, max_iter=K)
+        (a[:g.numel()] * g).sum().backward()
+        torch.cuda.synchronize()
+        peaks.append(torch.cuda.max_memory_allocated() - base)
+        del a, J
+    assert max(peaks) == min(peaks), peaks
