@@ -54,8 +54,9 @@ struct CtaGeo {
     const int R = nbl >= kCtaThreads ? 1 : (kCtaThreads / nbl < 16 ? kCtaThreads / nbl : 16);
     const int scr = R > 1 && 16 * nbl * R > 2 * kCtaThreads ? 16 * nbl * R : 2 * kCtaThreads;
     g.oRed = g.oScr + scr;
-    g.words = g.oRed + 8 * kCtaWarps + 8;  // block sums use [0, 2 warps); the
-                                            // factor's pivot flag [4 warps + 7]
+    g.words = g.oRed + 8 * kCtaWarps + 8;  // two reduction buffers [0, 4 warps),
+                                            // the factor's pivot flag [4 warps + 7],
+                                            // compaction counts [5 warps, 6 warps)
     return g;
   }
   __host__ __device__ size_t bytes() const { return ((size_t)words * 4 + 127) & ~(size_t)127; }
@@ -73,6 +74,7 @@ struct CtaSolver {
   uint32_t act_bits, fmask_bits;
   bool fmask_valid;
   float fmax, qmax;
+  int rb = 0;  // reduction buffer the next block reduction uses
 
   __device__ __forceinline__ float* Ms() { return sm + geo.oM; }
   __device__ __forceinline__ float* Ls() { return sm + geo.oL; }
@@ -90,23 +92,30 @@ struct CtaSolver {
   __device__ __forceinline__ bool row_valid(int u) const { return row(u) < m; }
 
   // ------------------------------------------------------ block reductions
-  // All threads call these (uniform control flow); each ends with a barrier
-  // so the reduction slots can be reused immediately.
+  // All threads call these (uniform control flow).  Consecutive reductions
+  // alternate between two slot buffers, so one barrier per reduction
+  // suffices: a thread can write a buffer again only after passing the next
+  // reduction's barrier, which every thread reaches only after reading this
+  // one's partials.
+  __device__ __forceinline__ float* red_buffer() {
+    float* R = Red() + rb * 2 * kCtaWarps;
+    rb ^= 1;
+    return R;
+  }
   __device__ __forceinline__ float block_sum(float v) {
     v = warp_sum(v);
-    float* R = Red();
+    float* R = red_buffer();
     if (lane == 0) R[warp] = v;
     __syncthreads();
     float t = 0.f;
 #pragma unroll
     for (int w = 0; w < kCtaWarps; ++w) t += R[w];
-    __syncthreads();
     return t;
   }
   __device__ __forceinline__ void block_sum2(float& a, float& b) {
     a = warp_sum(a);
     b = warp_sum(b);
-    float* R = Red();
+    float* R = red_buffer();
     if (lane == 0) {
       R[warp] = a;
       R[kCtaWarps + warp] = b;
@@ -118,19 +127,17 @@ struct CtaSolver {
       ta += R[w];
       tb += R[kCtaWarps + w];
     }
-    __syncthreads();
     a = ta;
     b = tb;
   }
   __device__ __forceinline__ float block_max(float v) {
     v = warp_max(v);
-    float* R = Red();
+    float* R = red_buffer();
     if (lane == 0) R[warp] = v;
     __syncthreads();
     float t = R[0];
 #pragma unroll
     for (int w = 1; w < kCtaWarps; ++w) t = fmaxf(t, R[w]);
-    __syncthreads();
     return t;
   }
   __device__ __forceinline__ bool block_any(bool p) {
@@ -594,7 +601,7 @@ struct CtaSolver {
     act_bits = 0;
     float* F = Fs();
     int* idx = Idx();
-    float* Rd = Red();
+    float* Rd = Red() + 5 * kCtaWarps;  // compaction counts (own slots)
     float fm = 0.f;
     int base = 0;
 #pragma unroll
