@@ -83,7 +83,7 @@ def case_from(p, name):
     return dict(name=name, nv=int(M.shape[0]), m=int(J.shape[0]), **ins, **out)
 
 
-def main():
+def build_document():
     cases = []
     # hand-worked two-DoF case: a = (-5/11, 12/11), w = (4/11, -3/11),
     # daref = 3/11, dJ = (63/121, -72/121)
@@ -103,7 +103,7 @@ def main():
             c = case_from(w.instance(b), f"{label}-{b}")
             if c["margin"] >= 1e-4:  # keep instances with no row near its boundary
                 cases.append(c)
-    doc = {
+    return {
         "what": "exact minimisers of Eq. 5 (pyramidal rows) and their Eq. 17 adjoints "
                 "for L = g^T a, by exact-rational enumeration of active sets",
         "written_by": "tests/golden/make_golden.py (no solver code used)",
@@ -111,6 +111,11 @@ def main():
                     "Eq. 17 (IFT adjoint)",
         "cases": cases,
     }
+
+
+def main():
+    doc = build_document()
+    cases = doc["cases"]
     out = os.path.join(HERE, "tiny_exact.json")
     with open(out, "w") as fh:
         json.dump(doc, fh, indent=0)

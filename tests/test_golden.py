@@ -26,6 +26,18 @@ def _rel(x, y):
     return float(np.max(np.abs(x - y)) / max(np.max(np.abs(y)), 1e-300))
 
 
+def test_fixture_is_what_its_script_writes():
+    # the stored values come from the committed exact-arithmetic script alone
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "make_golden", os.path.join(os.path.dirname(GOLDEN), "make_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with open(GOLDEN) as fh:
+        stored = json.load(fh)
+    assert json.loads(json.dumps(mod.build_document())) == stored
+
+
 def test_fixture_covers_the_cases_it_claims():
     cases = load_cases()
     names = [c["name"] for c in cases]
