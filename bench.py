@@ -53,11 +53,12 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0, period_ms=50):
+    def __init__(self, index=0, period_ms=20):
         self.index = index
         self.period_ms = period_ms
         self.proc = None
-        self.lines = []
+        self.lines = []   # (host monotonic time of arrival, csv line)
+        self.marks = {}
 
     def __enter__(self):
         try:
@@ -73,7 +74,16 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def wait_first(self, timeout=5.0):
+        """Block until nvidia-smi has printed its first sample (or timeout)."""
+        t_end = time.monotonic() + timeout
+        while self.proc is not None and not self.lines and time.monotonic() < t_end:
+            time.sleep(0.01)
+
+    def mark(self, name):
+        self.marks[name] = time.monotonic()
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -83,10 +93,16 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, start=None, end=None):
+        """Median SM clock, max clock and throttle reasons of the samples that
+        arrived between marks `start` and `end` (all samples if unset)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0 = self.marks.get(start, -1e300)
+        t1 = self.marks.get(end, 1e300)
+        for tt, ln in self.lines:
+            if not (t0 <= tt <= t1):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -163,19 +179,34 @@ def workload_config(name, w):
             "D_range": list(p["d_range"]), "seed": p["seed"]}
 
 
-def cpu_baseline(w, max_instances=None, threads=None):
-    """The FP64 oracle, as it stands, on the host cores."""
+def cpu_baseline(w, max_instances=None, threads=None, single_sample=2048):
+    """The FP64 oracle, as it stands, on the host cores: the whole sample on
+    every core (threads claim chunks of 64 instances), and the first
+    `single_sample` instances of it on one core.  Inputs are converted to the
+    oracle's float64 arrays before the clock starts."""
     import oracle
     threads = threads or (os.cpu_count() or 1)
     n = w.n if max_instances is None else min(w.n, max_instances)
     ws = w if n == w.n else w.subset(np.arange(n))
     oracle.build()
+    pw = oracle.PreparedWorkload(ws)
     t0 = time.perf_counter()
-    oracle.solve_workload(ws, threads=threads)
+    pw.run_all(threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {n} of the {w.n} instances, forward + adjoint, "
-                      f"{threads} threads, {dt:.2f} s wall"}
+    res = {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"first {n} of the {w.n} instances, forward + adjoint, "
+                     f"{threads} threads, {dt:.2f} s wall"}
+    if single_sample:
+        n1 = min(n, single_sample)
+        w1 = ws if n1 == ws.n else ws.subset(np.arange(n1))
+        p1 = oracle.PreparedWorkload(w1)
+        t0 = time.perf_counter()
+        p1.run_all(threads=1)
+        d1 = time.perf_counter() - t0
+        res["single_thread"] = {"value": n1 / d1, "unit": UNIT, "cores": 1,
+                                "sample": f"first {n1} instances, one thread, {d1:.2f} s wall"}
+    res["build"] = "gcc -O3 -march=native -std=c99 -ffp-contract=off"
+    return res
 
 
 def _serve_pool(n_requests, rate, seed, pool_per_class=2048):
@@ -292,27 +323,43 @@ def run_serve(args):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, each step one
+    cpu_baseline() pass over the same instances the GPU arm's cpu_baseline
+    leg times (the whole workload by default)."""
     ws_, rank = _dist()
     if rank != 0:
         return
     w = make_workload(args.workload, 0, args.n)
-    n_sample = args.ref_sample
-    vals = []
+    n_sample = min(w.n, args.cpu_sample)
     for _ in range(args.warmup):
-        cpu_baseline(w, max_instances=min(256, n_sample))
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(w, max_instances=n_sample))
+        cpu_baseline(w, max_instances=min(256, n_sample), single_sample=0)
+    vals = [cpu_baseline(w, max_instances=n_sample, single_sample=0)
+            for _ in range(args.steps)]
     v = statistics.median([x["value"] for x in vals])
+    one = cpu_baseline(w, max_instances=n_sample)["single_thread"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * n_sample / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.workload, w),
+            "data": "synthetic", "config": bench_config(args.workload, w),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"],
-                             "kind": "oracle", "sample": vals[0]["sample"]},
+                             "kind": "oracle", "sample": vals[0]["sample"]
+                             + f"; median of {args.steps} steps",
+                             "single_thread": one, "build": vals[0]["build"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def bench_config(name, w):
+    """The `config` object both arms print for a workload."""
+    return dict(workload_config(name, w),
+                l2="inputs+outputs 330 MB per step exceed the 126 MB L2; no flush",
+                graph="one CUDA-graph replay per step (plan)",
+                claim_order="per bucket, cost-descending, dynamic counter",
+                precision="FP32 with compensated residuals and refinement; parity "
+                          "1e-4 (a) / 1e-3 (gradients) relative to an FP64 oracle; "
+                          "the paper's experiments use FP64")
 
 
 def run_gpu(args):
@@ -342,10 +389,23 @@ def run_gpu(args):
         plan = solver.FusedPlan(batch, g, tol=args.tol, max_iter=args.max_iter,
                                 autotune=args.warps_per_block == 0, graph=True,
                                 warps_per_block=args.warps_per_block, out=out)
-        for _ in range(args.warmup):
-            plan.launch()
     torch.cuda.synchronize()
     plan_info = plan.describe()
+    # clocks are sampled from before the warm-up to the end of the timed
+    # region; the warm-up runs at least W steps and at least 0.5 s so that
+    # samples under this same load exist even when K steps take milliseconds
+    clk = ClockSampler(index=local).__enter__()
+    clk.wait_first()
+    clk.mark("warmup")
+    t_w = time.monotonic()
+    with torch.cuda.stream(stream):
+        n_w = 0
+        while n_w < args.warmup or time.monotonic() - t_w < 0.5:
+            plan.launch()
+            n_w += 1
+            if n_w % 16 == 0:
+                stream.synchronize()
+    torch.cuda.synchronize()
 
     # ---- timed region: K graph replays on `stream`
     def barrier():
@@ -355,14 +415,17 @@ def run_gpu(args):
 
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(index=local) as clk:
-        barrier()
-        with torch.cuda.stream(stream):
-            ev0.record(stream)
-            for _ in range(args.steps):
-                plan.launch()
-            ev1.record(stream)
-        barrier()
+    barrier()
+    clk.mark("timed")
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.launch()
+        ev1.record(stream)
+    barrier()
+    clk.mark("end")
+    time.sleep(0.05)   # the sample in flight at the end of the timed region
+    clk.__exit__(None, None, None)
     ms_total = ev0.elapsed_time(ev1)
     t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
     if world > 1:
@@ -417,11 +480,12 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(args.workload, w),
-                           l2="inputs+outputs 330 MB per step exceed the 126 MB L2; no flush",
-                           graph="one CUDA-graph replay per step (plan)",
-                           claim_order="per bucket, cost-descending, dynamic counter"),
-            "roofline": roof, "clocks": clk.summary(),
+            "config": bench_config(args.workload, w),
+            "roofline": roof,
+            "clocks": dict(clk.summary("warmup", "end"),
+                           window="nvidia-smi samples from the start of the warm-up "
+                                  f"({n_w} replays, >= 0.5 s) to the end of the timed region",
+                           timed_region=clk.summary("timed", "end")),
             "gpu_launches": args.steps * plan_info["kernels"], "plan": plan_info,
             "status_counts": np.bincount(status, minlength=6).tolist(),
             "iters_mean": float(iters.mean()), "iters_max": int(iters.max())}
@@ -681,7 +745,6 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=32768)
-    ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-ncg", action="store_true",
                     help="skip the conjugate-gradient forward solver leg")

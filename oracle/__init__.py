@@ -38,7 +38,6 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cs_oracle.c")
-_LIB = os.path.join(_HERE, "_cs_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -48,16 +47,42 @@ DEFAULT_TOL = 1e-12
 DEFAULT_MAX_ITER = 100
 
 
+def _host_signature() -> str:
+    """A short key of this host's CPU (model and instruction-set flags): the
+    library is compiled with -march=native, so a copy built on another machine
+    must not be loaded here."""
+    import hashlib
+    key = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith(("model name", "flags", "Features", "CPU part")):
+                    key += line
+                    if line.startswith(("flags", "Features")):
+                        break
+    except OSError:
+        pass
+    return hashlib.sha1(key.encode()).hexdigest()[:12]
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, f"_cs_oracle-{_host_signature()}.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle (gcc -O2, no fast-math) if it is missing or stale."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", _SRC,
+    """Compile the oracle (gcc -O3 -march=native, ISO C99: no FMA contraction
+    and no fast-math, so every result is the plain double-precision
+    evaluation of the source) if it is missing or stale for this host."""
+    lib = lib_path()
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= os.path.getmtime(_SRC)):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O3", "-march=native", "-std=c99",
+                           "-ffp-contract=off", "-fPIC", "-shared", _SRC,
                            "-o", tmp, "-lm"])
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 def _load():
@@ -401,6 +426,84 @@ def line_search_one(M, J, qfrc, aref, D, a, p):
                                         c(pp)))
 
 
+class PreparedWorkload:
+    """A packed batch converted once to the oracle's float64 / int arrays,
+    with its output arrays; ``run`` solves instances [lo, hi)."""
+
+    def __init__(self, w, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER, adjoint=True,
+                 theta=False):
+        self.lib = _load()
+        inst = w.inst
+        self.n = n = inst.shape[0]
+        self.nv = np.ascontiguousarray(inst["nv"], np.int32)
+        self.m = np.ascontiguousarray(inst["m"], np.int32)
+        self.offs = [np.ascontiguousarray(inst[k], np.int64)
+                     for k in ("off_M", "off_J", "off_v", "off_r")]
+        self.M, self.J, self.q, self.ar, self.D, self.g = (
+            np.ascontiguousarray(x, np.float64)
+            for x in (w.M, w.J, w.qfrc, w.aref, w.D, w.g))
+        self.tol, self.max_iter, self.adjoint, self.theta = tol, max_iter, adjoint, theta
+        self.a = np.zeros(max(self.q.size, 1))
+        self.dq = np.zeros(max(self.q.size, 1))
+        self.dr = np.zeros(max(self.ar.size, 1))
+        self.dJ = np.zeros(max(self.J.size, 1))
+        self.act = np.zeros(max(self.ar.size, 1), np.uint8)
+        self.dM = np.zeros(max(self.M.size, 1)) if theta else None
+        self.dD = np.zeros(max(self.ar.size, 1)) if theta else None
+        self.status = np.full(n, -1, np.int32)
+        self.iters = np.zeros(n, np.int32)
+        P = ctypes.POINTER
+        cd = lambda x: None if x is None else x.ctypes.data_as(P(ctypes.c_double))
+        ci32 = lambda x: x.ctypes.data_as(P(ctypes.c_int32))
+        ci64 = lambda x: x.ctypes.data_as(P(ctypes.c_int64))
+        # pointers taken once: a call of run() only crosses into the C code
+        self._ptrs = ([ci32(self.nv), ci32(self.m)] + [ci64(o) for o in self.offs]
+                      + [cd(self.M), cd(self.J), cd(self.q), cd(self.ar), cd(self.D),
+                         cd(self.g) if adjoint else None])
+        self._outs = [cd(self.a), self.act.ctypes.data_as(P(ctypes.c_uint8)),
+                      ci32(self.status), ci32(self.iters), cd(self.dq), cd(self.dr),
+                      cd(self.dJ), cd(self.dM), cd(self.dD)]
+
+    def run(self, lo, hi):
+        self.lib.oracle_batch(lo, hi, *self._ptrs, self.tol, self.max_iter, *self._outs)
+
+    def run_all(self, threads=1, chunk=64):
+        """Every instance, on `threads` host threads that claim chunks of
+        `chunk` consecutive instances from a shared counter (ctypes releases
+        the GIL during the C call, so the threads run in parallel)."""
+        n = self.n
+        if threads <= 1 or n <= chunk:
+            if n:
+                self.run(0, n)
+            return
+        lock = threading.Lock()
+        nxt = [0]
+
+        def worker():
+            while True:
+                with lock:
+                    lo = nxt[0]
+                    nxt[0] = lo + chunk
+                if lo >= n:
+                    return
+                self.run(lo, min(n, lo + chunk))
+
+        ts = [threading.Thread(target=worker) for _ in range(threads)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+
+    def outputs(self):
+        out = dict(a=self.a[:self.q.size], dqfrc=self.dq[:self.q.size],
+                   daref=self.dr[:self.ar.size], dJ=self.dJ[:self.J.size],
+                   act=self.act[:self.ar.size], status=self.status, iters=self.iters)
+        if self.theta:
+            out["dM"] = self.dM[:self.M.size]
+            out["dD"] = self.dD[:self.ar.size]
+        return out
+
+
 def solve_workload(w, idx=None, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
                    adjoint=True, threads=1, theta=False):
     """Forward (+ adjoint with the workload's g) for a packed ragged batch.
@@ -411,68 +514,24 @@ def solve_workload(w, idx=None, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
     instance).  With ``theta`` it adds dM (packed like M) and dD (packed like
     D), the remaining parameter gradients of Eq. 17.
     """
-    lib = _load()
-    inst = w.inst
-    n = inst.shape[0]
-    nv = np.ascontiguousarray(inst["nv"], np.int32)
-    m = np.ascontiguousarray(inst["m"], np.int32)
-    offs = [np.ascontiguousarray(inst[k], np.int64)
-            for k in ("off_M", "off_J", "off_v", "off_r")]
-    M, J, q, ar, D, g = (np.ascontiguousarray(x, np.float64)
-                         for x in (w.M, w.J, w.qfrc, w.aref, w.D, w.g))
-    a = np.zeros(max(q.size, 1))
-    dq = np.zeros(max(q.size, 1))
-    dr = np.zeros(max(ar.size, 1))
-    dJ = np.zeros(max(J.size, 1))
-    act = np.zeros(max(ar.size, 1), np.uint8)
-    dM = np.zeros(max(M.size, 1)) if theta else None
-    dD = np.zeros(max(ar.size, 1)) if theta else None
-    status = np.full(n, -1, np.int32)
-    iters = np.zeros(n, np.int32)
-    P = ctypes.POINTER
-    cd = lambda x: x.ctypes.data_as(P(ctypes.c_double))
-    ci32 = lambda x: x.ctypes.data_as(P(ctypes.c_int32))
-    ci64 = lambda x: x.ctypes.data_as(P(ctypes.c_int64))
-
-    def run(lo, hi):
-        lib.oracle_batch(lo, hi, ci32(nv), ci32(m), *[ci64(o) for o in offs],
-                         cd(M), cd(J), cd(q), cd(ar), cd(D),
-                         cd(g) if adjoint else None, tol, max_iter, cd(a),
-                         act.ctypes.data_as(P(ctypes.c_uint8)), ci32(status),
-                         ci32(iters), cd(dq), cd(dr), cd(dJ),
-                         cd(dM) if theta else None, cd(dD) if theta else None)
-
+    pw = PreparedWorkload(w, tol=tol, max_iter=max_iter, adjoint=adjoint, theta=theta)
     if idx is None:
-        ranges = []
-        chunk = max(1, (n + threads - 1) // max(threads, 1))
-        for lo in range(0, n, chunk):
-            ranges.append((lo, min(n, lo + chunk)))
+        pw.run_all(threads=threads)
     else:
-        ranges = [(int(b), int(b) + 1) for b in np.asarray(idx).ravel()]
-    if threads <= 1 or len(ranges) <= 1:
-        for lo, hi in ranges:
-            run(lo, hi)
-    else:
-        # ctypes releases the GIL during the C call, so plain threads give
-        # real parallelism over disjoint instance ranges.
-        if idx is not None:
-            parts = np.array_split(np.arange(len(ranges)), threads)
-            work = [[ranges[i] for i in p] for p in parts if len(p)]
+        sel = [int(b) for b in np.asarray(idx).ravel()]
+        if threads <= 1 or len(sel) <= 1:
+            for b in sel:
+                pw.run(b, b + 1)
         else:
-            work = [[r] for r in ranges]
+            parts = [p for p in np.array_split(np.asarray(sel), threads) if len(p)]
 
-        def worker(rs):
-            for lo, hi in rs:
-                run(lo, hi)
+            def worker(bs):
+                for b in bs:
+                    pw.run(int(b), int(b) + 1)
 
-        ts = [threading.Thread(target=worker, args=(rs,)) for rs in work]
-        for t in ts:
-            t.start()
-        for t in ts:
-            t.join()
-    out = dict(a=a[:q.size], dqfrc=dq[:q.size], daref=dr[:ar.size],
-               dJ=dJ[:J.size], act=act[:ar.size], status=status, iters=iters)
-    if theta:
-        out["dM"] = dM[:M.size]
-        out["dD"] = dD[:ar.size]
-    return out
+            ts = [threading.Thread(target=worker, args=(p,)) for p in parts]
+            for t in ts:
+                t.start()
+            for t in ts:
+                t.join()
+    return pw.outputs()

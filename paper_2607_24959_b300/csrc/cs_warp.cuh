@@ -43,6 +43,14 @@ constexpr int kAdjointRefineMax = 8;
 // refinement iteration has reached its attainable accuracy.
 constexpr float kStepTol = 1.0e-7f;
 constexpr float kForceTol = 1.0e-6f;
+// The adjoint's refinement stops once the next correction would move w by
+// <= kAdjStepTol |w| and the active lambda = D_act . J w by <= kAdjForceTol
+// |lambda|: that bounds the remaining error of every gradient two orders of
+// magnitude below the 1e-3 relative tolerance they are held to, without the
+// passes that only chase FP32 resolution.  (The forward keeps the tighter
+// pair above: a decides the active set, whose rows are compared one by one.)
+constexpr float kAdjStepTol = 1.0e-6f;
+constexpr float kAdjForceTol = 1.0e-5f;
 
 // ---------------------------------------------------------------- EFT helpers
 // __f*_rn intrinsics are never contracted into FMAs, which keeps the
@@ -96,20 +104,41 @@ __device__ __forceinline__ float warp_max(float v) {
 // compensated residual; f itself stays, the gradient writer reads it).  The
 // warp kernel's own modes use it; callers that keep f, its low part and
 // lambda live together (the unrolled reverse sweep, the round cone) do not.
+// Number of RA x 4 blocks (RA rows, an aligned quad of columns) that cover
+// the lower triangle of an NV x NV matrix.
+__host__ __device__ constexpr int quad_blocks(int NV, int RA) {
+  int n = 0;
+  for (int r0 = 0; r0 < NV; r0 += RA) n += ((r0 + RA < NV ? r0 + RA : NV) + 3) / 4;
+  return n;
+}
+// Rows per assembly block: the smallest of 1, 2, 4, 8 whose blocks fit 32 lanes.
+__host__ __device__ constexpr int quad_rows(int NV) {
+  return quad_blocks(NV, 1) <= 32 ? 1 : quad_blocks(NV, 2) <= 32 ? 2
+       : quad_blocks(NV, 4) <= 32 ? 4 : 8;
+}
+
 template <int NV, int MT, bool kShare = false>
 struct Geo {
   static_assert(NV >= 1 && NV <= 32, "one lane per row of H");
   static constexpr int MCAP = 32 * MT;               // rows per instance
-  static constexpr int BS = (NV + 6) / 7;            // H block edge
+  static constexpr int BS = (NV + 6) / 7;            // block edge of the round-cone assembly
   static constexpr int NB = (NV + BS - 1) / BS;      // blocks per edge (<= 7)
   static constexpr int NBLK = NB * (NB + 1) / 2;     // lower blocks (<= 28)
-  static constexpr int NVP = NB * BS;                // padded columns
-  static constexpr int JS = NVP | 1;                 // J row stride (odd)
+  // J rows hold NQ aligned quads of columns; the row stride is a multiple of
+  // four words whose quotient by four is odd, so that the 16-byte loads of
+  // eight consecutive lanes' rows (one shared-memory wavefront) fall in eight
+  // distinct bank quads, and columns walked by consecutive lanes are
+  // consecutive words.
+  static constexpr int NQ = (NV + 3) / 4;            // column quads
+  static constexpr int JS = 4 * ((NQ & 1) ? NQ : NQ + 1);  // J row stride
+  static constexpr int RA = quad_rows(NV);           // rows per assembly block
+  static constexpr int NABLK = quad_blocks(NV, RA);  // assembly blocks (<= 32)
+  static_assert(NABLK <= 32, "one lane per assembly block");
   static constexpr int MS = NV | 1;                  // M/L row stride (odd)
   // shared-memory slice of one warp, in 4-byte words
   static constexpr int oM = 0;                       // M   NV x MS
   static constexpr int oL = oM + NV * MS;            // H/L NV x MS
-  static constexpr int oJ = oL + NV * MS;            // J   MCAP x JS
+  static constexpr int oJ = (oL + NV * MS + 3) & ~3; // J   MCAP x JS (16-byte aligned)
   static constexpr int oD = oJ + MCAP * JS;          // D   MCAP
   static constexpr int oF = oD + MCAP;               // f   MCAP
   static constexpr int oLam = kShare ? oD : oF + MCAP;              // lambda = D_act J w
@@ -389,91 +418,57 @@ struct WarpSolver {
 
 
   // ------------------------------------------------------------- Cholesky
-  // Left-looking Cholesky of the lower rows in Ls(), in place.  At step k
-  // every lane j computes L[j][k] = H[j][k] - sum_{i<k} L[j][i] L[k][i]
-  // (equal trip counts, no divergence); lane k's value is the pivot.  The
-  // reciprocal pivots go to the V_DINV slot.  Returns false on a non-positive
-  // pivot.  The fp32 factor is only the preconditioner of a compensated
+  // Cholesky of the lower rows in Ls(), in place, with the matrix in
+  // registers: lane j loads row j of H, and for every column k (right-
+  // looking, unrolled) the pivot H_kk is broadcast from lane k, lane j forms
+  // L_jk = H_jk / L_kk, and the trailing entries of its row are updated,
+  // H_jc -= L_jk L_ck for c > k, with L_ck shuffled from lane c.  Every
+  // entry sees the same fused multiply-adds in the same order as the
+  // left-looking recurrence L_jc = (H_jc - sum_{i<c} L_ji L_ci) / L_cc, so the
+  // factor does not depend on the loop order.  Entries above the diagonal
+  // are carried along (loaded, updated and stored back) but never read by
+  // anything else, which saves a predicate per entry.  The reciprocal
+  // pivots go to the V_DINV slot.  Returns false on a non-positive or
+  // non-finite pivot: such a pivot makes its L_kk NaN (rsqrt of a negative
+  // number or of zero, times the pivot), so one test of the diagonal at the
+  // end finds it.  The fp32 factor only preconditions a compensated
   // iteration, so the reciprocal square root is the MUFU one.
   //
-  // Blocked by kFB columns: each lane forms its row's kFB partial dot
-  // products against the finished columns in one pass (kFB independent
-  // chains), the kFB x kFB diagonal block is gathered by shuffles and
-  // factored by every lane, and each lane finishes its own row of the block
-  // column; one warp barrier per block instead of two per column.
-  __device__ __forceinline__ bool factor() {
-    float* L = Ls();
-    float* dv = Vec(V_DINV);
-    float* Lj = L + min(lane, NV - 1) * G::MS;
-    bool ok = true;
-#pragma unroll 1
-    for (int kb = 0; kb < NV; kb += kFB) {
-      const float* Lb = L + kb * G::MS;
-      // H[j][kb+u] - sum_{i<kb} L[j][i] L[kb+u][i] (lanes j < kb+u read
-      // entries above the diagonal: their values are never used)
-      float acc[kFB];
+  // Not inlined: the unrolled body is NV (NV - 1) / 2 shuffle / fma pairs,
+  // and a copy per call site would crowd the instruction cache.
+  __device__ __noinline__ bool factor() {
+    float* Lj = Ls() + min(lane, NV - 1) * G::MS;
+    float h[NV];
 #pragma unroll
-      for (int u = 0; u < kFB; ++u) acc[u] = Lj[kb + u];
-#pragma unroll 1
-      for (int i = 0; i < kb; i += kFB) {
+    for (int c = 0; c < NV; ++c) h[c] = Lj[c];
+    float diag = 1.f;
+    // next pivot, H_kk after every update: lane k forms its own
+    // H_kk - L_k,k-1^2 without waiting for the shuffle that carries L_k,k-1
+    // to the other lanes (the same fma, so the same value), which keeps one
+    // shuffle and the MUFU off each column's critical path
+    float piv = h[0];
 #pragma unroll
-        for (int v = 0; v < kFB; ++v) {
-          const float x = Lj[i + v];
+    for (int k = 0; k < NV; ++k) {
+      const float d = __shfl_sync(kFull, piv, k);
+      const float rs = rsqrtf(d);
+      const float lkk = d * rs;
+      const float l = (lane == k) ? lkk : h[k] * rs;
+      h[k] = l;
+      diag = (lane == k) ? lkk : diag;
+      if (k + 1 < NV) piv = __fmaf_rn(-l, l, h[k + 1]);
 #pragma unroll
-          for (int u = 0; u < kFB; ++u) acc[u] = __fmaf_rn(-x, Lb[u * G::MS + i + v], acc[u]);
-        }
-      }
-      // the diagonal block, row kb+u of it from lane kb+u
-      float blk[kFB][kFB];
-#pragma unroll
-      for (int u = 0; u < kFB; ++u)
-#pragma unroll
-        for (int w = 0; w <= u; ++w) blk[u][w] = __shfl_sync(kFull, acc[w], kb + u);
-      float rs[kFB], lkk[kFB];
-#pragma unroll
-      for (int w = 0; w < kFB; ++w) {
-        float d = blk[w][w];
-#pragma unroll
-        for (int v = 0; v < w; ++v) d = __fmaf_rn(-blk[w][v], blk[w][v], d);
-        ok = ok && (d > 0.f) && (d < CUDART_INF_F);
-        rs[w] = rsqrtf(d);
-        lkk[w] = d * rs[w];
-#pragma unroll
-        for (int u = w + 1; u < kFB; ++u) {
-          float e = blk[u][w];
-#pragma unroll
-          for (int v = 0; v < w; ++v) e = __fmaf_rn(-blk[u][v], blk[w][v], e);
-          blk[u][w] = e * rs[w];
-        }
-        blk[w][w] = lkk[w];
-      }
-      // this lane's row of the block column
-      float out[kFB];
-#pragma unroll
-      for (int w = 0; w < kFB; ++w) {
-        float e = acc[w];
-#pragma unroll
-        for (int v = 0; v < w; ++v) e = __fmaf_rn(-out[v], blk[w][v], e);
-        out[w] = e * rs[w];
-      }
-      __syncwarp();
-      if (lane >= kb + kFB && lane < NV) {
-#pragma unroll
-        for (int w = 0; w < kFB; ++w) Lj[kb + w] = out[w];
-      }
-#pragma unroll
-      for (int u = 0; u < kFB; ++u) {
-        if (lane == kb + u) {
-#pragma unroll
-          for (int w = 0; w <= u; ++w) Lj[kb + w] = blk[u][w];
-          // the reciprocal pivot is derived from the stored diagonal, exactly
-          // as load_factor() does, so a kept factor solves bit-identically
-          dv[kb + u] = 1.0f / lkk[u];
-        }
-      }
-      __syncwarp();
+      for (int c = k + 1; c < NV; ++c) h[c] = __fmaf_rn(-l, __shfl_sync(kFull, l, c), h[c]);
     }
-    return ok;
+    __syncwarp();
+    if (lane < NV) {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) Lj[c] = h[c];
+      // the reciprocal pivot is derived from the stored diagonal, exactly as
+      // load_factor() does, so a kept factor solves bit-identically
+      Vec(V_DINV)[lane] = 1.0f / diag;
+    }
+    __syncwarp();
+    return !__any_sync(kFull, lane < NV && !(diag > 0.f && diag < CUDART_INF_F));
   }
 
   // z = (L L^T)^-1 x, vectors spread one element per lane.
@@ -487,7 +482,6 @@ struct WarpSolver {
   // column-at-a-time substitution, so the result is identical bit for bit;
   // the dependency chain has one shuffle per block instead of per column.
   static constexpr int kSB = (NV % 4 == 0) ? 4 : (NV % 3 == 0) ? 3 : (NV % 2 == 0) ? 2 : 1;
-  static constexpr int kFB = kSB;  // Cholesky block edge
   __device__ __forceinline__ float chol_solve(float x) {
     const float* L = Ls();
     const float* dinv = Vec(V_DINV);
@@ -548,65 +542,75 @@ struct WarpSolver {
   }
 
   // H = M + sum_{active} D_i J_i^T J_i (Eq. 9) into Ls(), then factor.
-  // Lane l < NBLK accumulates one BS x BS block of the lower triangle.
+  // Lane l < NABLK accumulates one RA x 4 block of the lower triangle (RA
+  // rows from RA*g, an aligned quad of columns), reading a row's quad with
+  // one 16-byte load; every entry sums its terms in active-row order.
   __device__ __forceinline__ bool assemble_and_factor() {
     const float* Mm = Ms();
     const float* Jm = Js();
     const float* Dm = Ds();
     const int* idx = Idx();
     float* L = Ls();
-    if (lane < G::NBLK) {
-      int bj = 0;
-      while ((bj + 1) * (bj + 2) / 2 <= lane) ++bj;
-      const int bk = lane - bj * (bj + 1) / 2;
-      float acc[G::BS][G::BS];
+    constexpr int RA = G::RA;
+    if (lane < G::NABLK) {
+      int g = 0, qd = lane;
+#pragma unroll 1
+      while (true) {
+        const int nq = (min(RA * (g + 1), NV) + 3) / 4;
+        if (qd < nq) break;
+        qd -= nq;
+        ++g;
+      }
+      const int r0 = RA * g, c0 = 4 * qd;
+      float acc[RA][4];
 #pragma unroll
-      for (int u = 0; u < G::BS; ++u)
+      for (int u = 0; u < RA; ++u)
 #pragma unroll
-        for (int v = 0; v < G::BS; ++v) acc[u][v] = 0.f;
-      const int cj = bj * G::BS, ck = bk * G::BS;
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
       // two rows per pass: their loads issue back to back
       int q = 0;
 #pragma unroll 1
       for (; q + 2 <= nact; q += 2) {
-        float x[2][G::BS], y[2][G::BS];
+        float x[2][RA];
+        float4 y[2];
 #pragma unroll
         for (int r2 = 0; r2 < 2; ++r2) {
           const int i = idx[q + r2];
           const float d = Dm[i];
           const float* Ji = Jm + i * G::JS;
 #pragma unroll
-          for (int u = 0; u < G::BS; ++u) x[r2][u] = Ji[cj + u] * d;
-#pragma unroll
-          for (int v = 0; v < G::BS; ++v) y[r2][v] = Ji[ck + v];
+          for (int u = 0; u < RA; ++u) x[r2][u] = Ji[r0 + u] * d;
+          y[r2] = *reinterpret_cast<const float4*>(Ji + c0);
         }
 #pragma unroll
         for (int r2 = 0; r2 < 2; ++r2)
 #pragma unroll
-          for (int u = 0; u < G::BS; ++u)
-#pragma unroll
-            for (int v = 0; v < G::BS; ++v)
-              acc[u][v] = __fmaf_rn(x[r2][u], y[r2][v], acc[u][v]);
+          for (int u = 0; u < RA; ++u) {
+            acc[u][0] = __fmaf_rn(x[r2][u], y[r2].x, acc[u][0]);
+            acc[u][1] = __fmaf_rn(x[r2][u], y[r2].y, acc[u][1]);
+            acc[u][2] = __fmaf_rn(x[r2][u], y[r2].z, acc[u][2]);
+            acc[u][3] = __fmaf_rn(x[r2][u], y[r2].w, acc[u][3]);
+          }
       }
       if (q < nact) {
         const int i = idx[q];
         const float d = Dm[i];
         const float* Ji = Jm + i * G::JS;
-        float x[G::BS], y[G::BS];
+        const float4 y = *reinterpret_cast<const float4*>(Ji + c0);
 #pragma unroll
-        for (int u = 0; u < G::BS; ++u) x[u] = Ji[cj + u] * d;
-#pragma unroll
-        for (int v = 0; v < G::BS; ++v) y[v] = Ji[ck + v];
-#pragma unroll
-        for (int u = 0; u < G::BS; ++u)
-#pragma unroll
-          for (int v = 0; v < G::BS; ++v) acc[u][v] = __fmaf_rn(x[u], y[v], acc[u][v]);
+        for (int u = 0; u < RA; ++u) {
+          const float x = Ji[r0 + u] * d;
+          acc[u][0] = __fmaf_rn(x, y.x, acc[u][0]);
+          acc[u][1] = __fmaf_rn(x, y.y, acc[u][1]);
+          acc[u][2] = __fmaf_rn(x, y.z, acc[u][2]);
+          acc[u][3] = __fmaf_rn(x, y.w, acc[u][3]);
+        }
       }
 #pragma unroll
-      for (int u = 0; u < G::BS; ++u)
+      for (int u = 0; u < RA; ++u)
 #pragma unroll
-        for (int v = 0; v < G::BS; ++v) {
-          const int rr = cj + u, cc = ck + v;
+        for (int v = 0; v < 4; ++v) {
+          const int rr = r0 + u, cc = c0 + v;
           if (rr < NV && cc <= rr) L[rr * G::MS + cc] = Mm[rr * G::MS + cc] + acc[u][v];
         }
     }
@@ -623,18 +627,29 @@ struct WarpSolver {
   }
 
   // ------------------------------------------------- compensated products
-  // s[t] + c[t] = J_i . (vh + vl) for the rows of this lane.
+  // s[t] + c[t] = J_i . (vh + vl) for the rows of this lane.  The vectors are
+  // broadcast slots (16-byte aligned, zero beyond NV); J rows and vectors are
+  // read a quad of columns at a time, and the terms are accumulated in column
+  // order.
   __device__ __forceinline__ void rows_dot2(const float* vh, const float* vl, float (&s)[MT],
                                             float (&c)[MT]) {
-    const float* Jm = Js() + lane * G::JS;
+    const float4* Jm = reinterpret_cast<const float4*>(Js() + lane * G::JS);
+    const float4* vh4 = reinterpret_cast<const float4*>(vh);
+    const float4* vl4 = reinterpret_cast<const float4*>(vl);
 #pragma unroll
     for (int t = 0; t < MT; ++t) { s[t] = 0.f; c[t] = 0.f; }
-#pragma unroll (kSB)
-    for (int k = 0; k < NV; ++k) {
-      const float xh = vh[k], xl = vl[k];
+#pragma unroll 1
+    for (int q = 0; q < G::NQ; ++q) {
+      const float4 xh = vh4[q], xl = vl4[q];
 #pragma unroll
       for (int t = 0; t < MT; ++t)
-        if (32 * t < m) dot2(s[t], c[t], Jm[32 * t * G::JS + k], xh, xl);
+        if (32 * t < m) {
+          const float4 j = Jm[8 * t * G::JS + q];
+          dot2(s[t], c[t], j.x, xh.x, xl.x);
+          dot2(s[t], c[t], j.y, xh.y, xl.y);
+          dot2(s[t], c[t], j.z, xh.z, xl.z);
+          dot2(s[t], c[t], j.w, xh.w, xl.w);
+        }
     }
   }
 
@@ -650,6 +665,26 @@ struct WarpSolver {
     c = 0.f;
     if (lane < NV) {
       int q = 0;
+      // four rows per pass, their loads issued before the arithmetic; rows
+      // q, q+2 go to one accumulator pair and q+1, q+3 to the other, as in
+      // a two-row pass
+#pragma unroll 1
+      for (; q + 3 < nact; q += 4) {
+        int i[4];
+        float x[4], y[4], z[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) i[u] = idx[q + u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          x[u] = Jm[i[u] * G::JS + lane];
+          y[u] = v[i[u]];
+          z[u] = vlo[i[u]];
+        }
+        dot2(s, c, x[0], y[0], z[0]);
+        dot2(s2, c2, x[1], y[1], z[1]);
+        dot2(s, c, x[2], y[2], z[2]);
+        dot2(s2, c2, x[3], y[3], z[3]);
+      }
 #pragma unroll 1
       for (; q + 1 < nact; q += 2) {
         const int i0 = idx[q], i1 = idx[q + 1];
@@ -684,15 +719,22 @@ struct WarpSolver {
 
   // Plain FP32 counterparts, used while the active set is still changing.
   __device__ __forceinline__ void rows_dot(const float* vh, float (&s)[MT]) {
-    const float* Jm = Js() + lane * G::JS;
+    const float4* Jm = reinterpret_cast<const float4*>(Js() + lane * G::JS);
+    const float4* v4 = reinterpret_cast<const float4*>(vh);
 #pragma unroll
     for (int t = 0; t < MT; ++t) s[t] = 0.f;
-#pragma unroll (kSB)
-    for (int k = 0; k < NV; ++k) {
-      const float xh = vh[k];
+#pragma unroll
+    for (int q = 0; q < G::NQ; ++q) {
+      const float4 x = v4[q];
 #pragma unroll
       for (int t = 0; t < MT; ++t)
-        if (32 * t < m) s[t] = __fmaf_rn(Jm[32 * t * G::JS + k], xh, s[t]);
+        if (32 * t < m) {
+          const float4 j = Jm[8 * t * G::JS + q];
+          s[t] = __fmaf_rn(j.x, x.x, s[t]);
+          s[t] = __fmaf_rn(j.y, x.y, s[t]);
+          s[t] = __fmaf_rn(j.z, x.z, s[t]);
+          s[t] = __fmaf_rn(j.w, x.w, s[t]);
+        }
     }
   }
   __device__ __forceinline__ float jt_active_plain(const float* v) {
@@ -701,6 +743,22 @@ struct WarpSolver {
     float s = 0.f, s2 = 0.f;
     if (lane < NV) {
       int q = 0;
+#pragma unroll 1
+      for (; q + 3 < nact; q += 4) {
+        int i[4];
+        float x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) i[u] = idx[q + u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          x[u] = Jm[i[u] * G::JS + lane];
+          y[u] = v[i[u]];
+        }
+        s = __fmaf_rn(x[0], y[0], s);
+        s2 = __fmaf_rn(x[1], y[1], s2);
+        s = __fmaf_rn(x[2], y[2], s);
+        s2 = __fmaf_rn(x[3], y[3], s2);
+      }
 #pragma unroll 1
       for (; q + 1 < nact; q += 2) {
         const int i0 = idx[q], i1 = idx[q + 1];
@@ -820,20 +878,9 @@ struct WarpSolver {
   template <bool kDiff = false>
   __device__ __forceinline__ float line_search(float p, float* dfmax, bool* crossed) {
     put_vec(V_P, p);
-    const float* Jm = Js() + lane * G::JS;
     const float* vp = Vec(V_P);
-#pragma unroll
-    for (int t = 0; t < MT; ++t) s_r[t] = 0.f;
-    float Mp = 0.f;
-    const float* Mr = Ms() + min(lane, NV - 1) * G::MS;
-#pragma unroll (kSB)
-    for (int k = 0; k < NV; ++k) {
-      const float pk = vp[k];
-#pragma unroll
-      for (int t = 0; t < MT; ++t)
-        if (32 * t < m) s_r[t] = __fmaf_rn(Jm[32 * t * G::JS + k], pk, s_r[t]);
-      Mp = __fmaf_rn(Mr[k], pk, Mp);
-    }
+    rows_dot(vp, s_r);
+    const float Mp = m_times_plain(vp);
     const float pMp = warp_sum(lane < NV ? p * Mp : 0.f);
     float c0;
     if (kDiff) {
@@ -919,6 +966,22 @@ struct WarpSolver {
     vl = __fsub_rn(lo, __fsub_rn(vh, s));
   }
 
+  // Whether the correction z (spread per lane) would move a by at most
+  // kStepTol amax and every active force D_i (J z)_i by at most kForceTol
+  // fmax (fmax from the last compensated residual).  Uses the V_X slot.
+  __device__ __forceinline__ bool small_correction(float z, float amax) {
+    const float zm = warp_max(fabsf(z));
+    if (!(zm <= kStepTol * amax)) return false;
+    put_vec(V_X, z);
+    float sz[MT];
+    rows_dot(Vec(V_X), sz);
+    float df = 0.f;
+#pragma unroll
+    for (int t = 0; t < MT; ++t)
+      if ((act_bits >> t) & 1u) df = fmaxf(df, fabsf(D_r[t] * sz[t]));
+    return warp_max(df) <= kForceTol * fmax;
+  }
+
   // --------------------------------------------------------- forward solve
   // Newton iteration (Eqs. 9-10) from a0 = M^-1 qfrc (Eq. 1).  Returns the
   // status; *iters = Newton steps.  On return the residual quantities (jar,
@@ -955,7 +1018,6 @@ struct WarpSolver {
       }
       if (rmax <= P.tol * scale) return CS_ST_OK;
       const bool same = !__any_sync(kFull, act_bits != prev_bits);
-      if (k > 0 && same && prev_small) return CS_ST_OK;
       if (k >= P.max_iter) return CS_ST_MAXITER;
       cg = cg && same;
       if (need_refactor()) {
@@ -963,6 +1025,18 @@ struct WarpSolver {
         cg = false;
       }
       const float z = chol_solve(r);
+      const float amax = warp_max(fabsf(ah));
+      // Once the active set has settled (compensated phase, the same set as
+      // at the previous point), the FP32 Newton correction z = H^-1 r
+      // estimates the remaining error of a: when it would move a by <=
+      // kStepTol |a| and every active force by <= kForceTol |f|, a is at the
+      // attainable FP32 accuracy and is returned as it is (its residual
+      // quantities are the ones just evaluated).
+      // A step just taken that was itself that small (a conjugated or
+      // stagnating direction whose line search found only a tiny alpha) ends
+      // the solve the same way.
+      if (precise && k > 0 && same && (prev_small || small_correction(z, amax)))
+        return CS_ST_OK;
       const float zr = warp_sum(z * r);
       const float beta = (cg && zr_prev > 0.f) ? fmaxf(zr / zr_prev, 0.f) : 0.f;
       float p = __fmaf_rn(beta, p_prev, -z);
@@ -971,7 +1045,6 @@ struct WarpSolver {
         p = -z;
         ptr = -zr;
       }
-      const float amax = warp_max(fabsf(ah));
       if (!(ptr < 0.f)) {
         const float pm = warp_max(fabsf(p));
         return (pm <= kStepTol * amax) ? CS_ST_OK : CS_ST_NOPROGRESS;
@@ -982,8 +1055,7 @@ struct WarpSolver {
       const float dp = alpha * p;
       add_to_pair(ah, al, dp);
       *iters = k + 1;
-      const float smax = warp_max(fabsf(dp));
-      prev_small = precise && (smax <= kStepTol * amax) && (dfm <= kForceTol * fmax);
+      prev_small = precise && (warp_max(fabsf(dp)) <= kStepTol * amax) && (dfm <= kForceTol * fmax);
       prev_bits = act_bits;
       cg = precise && !crossed;
       p_prev = p;
@@ -1058,30 +1130,39 @@ struct WarpSolver {
   // Solve H w = g at the current point (Eq. 17) by iterative refinement with
   // compensated residuals.  Leaves w in (wh, wl), lambda = D_act . J w in
   // Lam() for every row < m.
-  __device__ __forceinline__ void adjoint(float& wh, float& wl) { solve_refined(gj, 0.f, wh, wl); }
+  __device__ __forceinline__ void adjoint(float& wh, float& wl) {
+    solve_refined(gj, 0.f, wh, wl, kAdjStepTol, kAdjForceTol);
+  }
 
   // H w = rhs + rhs_lo (spread per lane) with H = M + sum over the active
   // list of D_i J_i^T J_i factored in Ls(): FP32 factor as preconditioner,
   // residuals rhs - M w - J^T (D_act . J w) accumulated with error-free
   // transformations.
-  __device__ __forceinline__ void solve_refined(float rhs, float rhs_lo, float& wh, float& wl) {
+  //
+  // Each pass forms lambda = D_act . J w (compensated) at the current w, then
+  // the residual rho and the correction dw = H^-1 rho; when dw would move w
+  // by <= step_tol |w| and every active lambda by <= force_tol |lambda|, w is
+  // kept as it is (its error is bounded by the untaken correction) and lambda
+  // already belongs to it, so no pass is spent re-evaluating lambda at a
+  // point that differs from w only beyond that resolution.  The default pair
+  // is the forward's (FP32 resolution), which the unrolled reverse sweep
+  // needs; the IFT adjoint passes the looser kAdjStepTol / kAdjForceTol.
+  __device__ __forceinline__ void solve_refined(float rhs, float rhs_lo, float& wh, float& wl,
+                                                float step_tol = kStepTol,
+                                                float force_tol = kForceTol) {
     wh = chol_solve(rhs);
     wl = 0.f;
     float* Lm = Lam();
     float* Lml = Lamlo();
-    float lam_prev[MT];
-#pragma unroll
-    for (int t = 0; t < MT; ++t) lam_prev[t] = 0.f;
-    float dmax_prev = CUDART_INF_F;
 #pragma unroll 1
-    for (int it = 0; it <= kAdjointRefineMax; ++it) {
+    for (int it = 0;; ++it) {
       put_vec(V_WH, wh);
       put_vec(V_WL, wl);
       const float* vh = Vec(V_WH);
       const float* vl = Vec(V_WL);
       float s[MT], c[MT];
       rows_dot2(vh, vl, s, c);
-      float lmax = 0.f, dl = 0.f;
+      float lmax = 0.f;
 #pragma unroll
       for (int t = 0; t < MT; ++t) {
         if (32 * t < m) {
@@ -1095,19 +1176,11 @@ struct WarpSolver {
             Lml[lane + 32 * t] = lamlo;
           }
           lmax = fmaxf(lmax, fabsf(lam));
-          dl = fmaxf(dl, fabsf(lam - lam_prev[t]));
-          lam_prev[t] = lam;
         }
       }
       lmax = warp_max(lmax);
-      dl = warp_max(dl);
       __syncwarp();
-      if (it > 0) {
-        const float wmax = warp_max(fabsf(wh));
-        if ((dmax_prev <= kStepTol * wmax && dl <= kForceTol * lmax) ||
-            it == kAdjointRefineMax)
-          break;
-      }
+      if (it == kAdjointRefineMax) break;
       // rho = g - M w - J^T lambda (compensated)
       float js, jc, ms, mc;
       jt_active(Lm, Lml, js, jc);
@@ -1118,7 +1191,18 @@ struct WarpSolver {
       float rho = __fadd_rn(t2, __fsub_rn(__fadd_rn(__fadd_rn(e1, e2), rhs_lo), __fadd_rn(mc, jc)));
       if (lane >= NV) rho = 0.f;
       const float dw = chol_solve(rho);
-      dmax_prev = warp_max(fabsf(dw));
+      // the correction's size, in w and in the active lambda = D (J dw)
+      put_vec(V_X, dw);
+      float sd[MT];
+      rows_dot(Vec(V_X), sd);
+      float dl = 0.f;
+#pragma unroll
+      for (int t = 0; t < MT; ++t)
+        if ((act_bits >> t) & 1u) dl = fmaxf(dl, fabsf(D_r[t] * sd[t]));
+      const float dmax = warp_max(fabsf(dw));
+      const float wmax = warp_max(fabsf(wh));
+      dl = warp_max(dl);
+      if (dmax <= step_tol * wmax && dl <= force_tol * lmax) break;
       add_to_pair(wh, wl, dw);
     }
     __syncwarp();

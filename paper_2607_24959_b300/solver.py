@@ -439,7 +439,8 @@ class FusedPlan:
                              "instances": info.instances[i],
                              "warps_per_block": info.warps_per_block[i],
                              "kernel": "cta" if info.cta[i] else "warp",
-                             "tuned_ms": round(float(info.tuned_ms[i]), 4)} for i in range(k)]}
+                             "tuned_ms": round(float(info.tuned_ms[i]), 4)}
+                            for i in range(k)]}
 
     def close(self):
         if getattr(self, "_h", None):
