@@ -31,6 +31,8 @@
 #include <math_constants.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "contact_solve.h"
 
 namespace csk {
@@ -124,13 +126,12 @@ struct Geo {
   static constexpr int BS = (NV + 6) / 7;            // block edge of the round-cone assembly
   static constexpr int NB = (NV + BS - 1) / BS;      // blocks per edge (<= 7)
   static constexpr int NBLK = NB * (NB + 1) / 2;     // lower blocks (<= 28)
-  // J rows hold NQ aligned quads of columns; the row stride is a multiple of
-  // four words whose quotient by four is odd, so that the 16-byte loads of
-  // eight consecutive lanes' rows (one shared-memory wavefront) fall in eight
-  // distinct bank quads, and columns walked by consecutive lanes are
-  // consecutive words.
-  static constexpr int NQ = (NV + 3) / 4;            // column quads
-  static constexpr int JS = 4 * ((NQ & 1) ? NQ : NQ + 1);  // J row stride
+  // J rows hold NP pairs of columns; the row stride is twice an odd number,
+  // so that the 8-byte loads of sixteen consecutive lanes' rows (one
+  // shared-memory wavefront) fall in sixteen distinct bank pairs, and columns
+  // walked by consecutive lanes are consecutive words.
+  static constexpr int NP = (NV + 1) / 2;            // column pairs
+  static constexpr int JS = 2 * (NP | 1);            // J row stride
   static constexpr int RA = quad_rows(NV);           // rows per assembly block
   static constexpr int NABLK = quad_blocks(NV, RA);  // assembly blocks (<= 32)
   static_assert(NABLK <= 32, "one lane per assembly block");
@@ -144,10 +145,16 @@ struct Geo {
   static constexpr int oLam = kShare ? oD : oF + MCAP;              // lambda = D_act J w
   static constexpr int oFlo = kShare ? oF + MCAP : oLam + MCAP;     // low parts of f ...
   static constexpr int oLamlo = kShare ? oFlo : oFlo + MCAP;        // ... and of lambda
-  static constexpr int oIdx = oLamlo + MCAP;         // active rows (int)
-  static constexpr int oVec = oIdx + MCAP;           // broadcast vectors
+  static constexpr int oIdx = oLamlo + MCAP;         // active rows (bytes if kShare, else int)
+  static constexpr int oVec = oIdx + (kShare ? MCAP / 4 : MCAP);  // broadcast vectors
   static constexpr int kVec = kShare ? 4 : 7;        // broadcast slots (below)
-  static constexpr int kWords = oVec + kVec * 32;
+  // kShare (the warp kernel's modes): the assembled Newton matrix of the
+  // factored active set is kept, so that the next one is formed from the
+  // rows that entered or left the set (below), with a list of those rows
+  static constexpr int kChg = 32;                    // changed rows per update
+  static constexpr int oH = oVec + kVec * 32;        // H   NV x MS (kShare)
+  static constexpr int oChg = oH + (kShare ? NV * MS : 0);
+  static constexpr int kWords = oChg + (kShare ? kChg : 0);
   static constexpr int kBytes = ((kWords * 4) + 127) & ~127;
 };
 
@@ -189,6 +196,8 @@ struct WarpSolver {
   uint32_t act_bits;    // bit t: row lane+32t active at the current point
   uint32_t fmask_bits;  // active set the factor in Ls() belongs to
   bool fmask_valid;
+  uint32_t hmask_bits;  // active set the matrix in Hs() belongs to (kShare)
+  bool hmask_valid;
   int nact;
   // element registers (lane j < NV)
   float ah, al;          // a = ah + al
@@ -200,13 +209,18 @@ struct WarpSolver {
 
   __device__ __forceinline__ float* Ms() { return sm + G::oM; }
   __device__ __forceinline__ float* Ls() { return sm + G::oL; }
+  __device__ __forceinline__ float* Hs() { return sm + G::oH; }
+  __device__ __forceinline__ int* Chg() { return reinterpret_cast<int*>(sm + G::oChg); }
   __device__ __forceinline__ float* Js() { return sm + G::oJ; }
   __device__ __forceinline__ float* Ds() { return sm + G::oD; }
   __device__ __forceinline__ float* Fs() { return sm + G::oF; }
   __device__ __forceinline__ float* Lam() { return sm + G::oLam; }
   __device__ __forceinline__ float* Flo() { return sm + G::oFlo; }
   __device__ __forceinline__ float* Lamlo() { return sm + G::oLamlo; }
-  __device__ __forceinline__ int* Idx() { return reinterpret_cast<int*>(sm + G::oIdx); }
+  // Active-row list: row numbers < MCAP <= 256 fit a byte in the warp
+  // kernel's layout; the round cone and the unrolled sweep keep ints.
+  using idx_t = typename std::conditional<kShare, uint8_t, int>::type;
+  __device__ __forceinline__ idx_t* Idx() { return reinterpret_cast<idx_t*>(sm + G::oIdx); }
   // Broadcast slot of vector s.  kShare: w's pair takes the slots of p and of
   // a's low part, and the gradient writer's copy of a the slot of a's high
   // part (it holds the same value): in the warp kernel's modes the adjoint
@@ -281,6 +295,7 @@ struct WarpSolver {
   __device__ __forceinline__ bool load(const Params& P, const cs_inst& e) {
     nv = e.nv;
     m = e.m;
+    hmask_valid = false;
     if (!in_bounds(P, e)) return false;
     if constexpr (NV >= 16 || MT >= 3) {
       load_async(P, e);
@@ -434,13 +449,17 @@ struct WarpSolver {
   // end finds it.  The fp32 factor only preconditions a compensated
   // iteration, so the reciprocal square root is the MUFU one.
   //
+  // The matrix is read from src (rows of stride MS: Ls() itself, M, or the
+  // kept Newton matrix) and the factor written to Ls().
+  //
   // Not inlined: the unrolled body is NV (NV - 1) / 2 shuffle / fma pairs,
   // and a copy per call site would crowd the instruction cache.
-  __device__ __noinline__ bool factor() {
+  __device__ __noinline__ bool factor(const float* src = nullptr) {
     float* Lj = Ls() + min(lane, NV - 1) * G::MS;
+    const float* Sj = (src ? src : Ls()) + min(lane, NV - 1) * G::MS;
     float h[NV];
 #pragma unroll
-    for (int c = 0; c < NV; ++c) h[c] = Lj[c];
+    for (int c = 0; c < NV; ++c) h[c] = Sj[c];
     float diag = 1.f;
     // next pivot, H_kk after every update: lane k forms its own
     // H_kk - L_k,k-1^2 without waiting for the shuffle that carries L_k,k-1
@@ -531,94 +550,183 @@ struct WarpSolver {
 
   // Cholesky of M (the factor for the empty active set).
   __device__ __forceinline__ bool factor_M() {
-    const float* Mm = Ms();
-    float* L = Ls();
-    if (lane < NV) {
-#pragma unroll 1
-      for (int k = 0; k <= lane; ++k) L[lane * G::MS + k] = Mm[lane * G::MS + k];
-    }
-    __syncwarp();
-    return factor();
+    hmask_valid = false;
+    return factor(Ms());
   }
 
-  // H = M + sum_{active} D_i J_i^T J_i (Eq. 9) into Ls(), then factor.
-  // Lane l < NABLK accumulates one RA x 4 block of the lower triangle (RA
-  // rows from RA*g, an aligned quad of columns), reading a row's quad with
-  // one 16-byte load; every entry sums its terms in active-row order.
-  __device__ __forceinline__ bool assemble_and_factor() {
-    const float* Mm = Ms();
+  // H = M + sum_{active} D_i J_i^T J_i (Eq. 9), then its Cholesky factor in
+  // Ls().  Lane l < NABLK owns one RA x 4 block of the lower triangle (RA
+  // rows from RA*g, an aligned quad of columns) and reads a row's quad with
+  // one 16-byte load; every entry sums its terms in row-list order.
+  //
+  // kShare: H is kept in Hs() with the active set it belongs to, and the next
+  // one is formed from the rows that changed side, H += D_i J_i^T J_i for a
+  // row that entered and -= for one that left, when there are at most kChg
+  // of them and at most a quarter of the active count (else H is rebuilt
+  // from M).  A Newton step changes a few rows of the set (a median of four
+  // on the benchmark batch), so this replaces most of the assembly.  The
+  // rounding of such an update is that of adding or removing one row's
+  // terms, the same order as the rounding of a full assembly of the set, so
+  // the factor stays an equally good preconditioner; a factor that fails
+  // after an update is retried from a full assembly.
+  __device__ __forceinline__ int assembly_block(int& r0, int& c0) const {
+    int g = 0, qd = lane;
+#pragma unroll 1
+    while (true) {
+      const int nq = (min(G::RA * (g + 1), NV) + 3) / 4;
+      if (qd < nq) break;
+      qd -= nq;
+      ++g;
+    }
+    r0 = G::RA * g;
+    c0 = 4 * qd;
+    return g;
+  }
+
+  // acc += sum over list entries of s_i D_i J_i[r0..] J_i[c0..c0+3]^T, with
+  // s_i = -1 for entries marked by the top bit.
+  template <bool kSigned, typename T>
+  __device__ __forceinline__ void accumulate_rows(const T* list, int n, int r0, int c0,
+                                                  float (&acc)[G::RA][4]) {
+    constexpr int RA = G::RA;
     const float* Jm = Js();
     const float* Dm = Ds();
-    const int* idx = Idx();
-    float* L = Ls();
-    constexpr int RA = G::RA;
-    if (lane < G::NABLK) {
-      int g = 0, qd = lane;
+    int q = 0;
+    // two rows per pass: their loads issue back to back
 #pragma unroll 1
-      while (true) {
-        const int nq = (min(RA * (g + 1), NV) + 3) / 4;
-        if (qd < nq) break;
-        qd -= nq;
-        ++g;
-      }
-      const int r0 = RA * g, c0 = 4 * qd;
-      float acc[RA][4];
+    for (; q + 2 <= n; q += 2) {
+      float x[2][RA];
+      float4 y[2];
 #pragma unroll
-      for (int u = 0; u < RA; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-      // two rows per pass: their loads issue back to back
-      int q = 0;
-#pragma unroll 1
-      for (; q + 2 <= nact; q += 2) {
-        float x[2][RA];
-        float4 y[2];
-#pragma unroll
-        for (int r2 = 0; r2 < 2; ++r2) {
-          const int i = idx[q + r2];
-          const float d = Dm[i];
-          const float* Ji = Jm + i * G::JS;
-#pragma unroll
-          for (int u = 0; u < RA; ++u) x[r2][u] = Ji[r0 + u] * d;
-          y[r2] = *reinterpret_cast<const float4*>(Ji + c0);
-        }
-#pragma unroll
-        for (int r2 = 0; r2 < 2; ++r2)
-#pragma unroll
-          for (int u = 0; u < RA; ++u) {
-            acc[u][0] = __fmaf_rn(x[r2][u], y[r2].x, acc[u][0]);
-            acc[u][1] = __fmaf_rn(x[r2][u], y[r2].y, acc[u][1]);
-            acc[u][2] = __fmaf_rn(x[r2][u], y[r2].z, acc[u][2]);
-            acc[u][3] = __fmaf_rn(x[r2][u], y[r2].w, acc[u][3]);
-          }
-      }
-      if (q < nact) {
-        const int i = idx[q];
-        const float d = Dm[i];
+      for (int r2 = 0; r2 < 2; ++r2) {
+        const int e = list[q + r2];
+        const int i = kSigned ? (e & 0x7fffffff) : e;
+        const float d = (kSigned && e < 0) ? -Dm[i] : Dm[i];
         const float* Ji = Jm + i * G::JS;
-        const float4 y = *reinterpret_cast<const float4*>(Ji + c0);
+#pragma unroll
+        for (int u = 0; u < RA; ++u) x[r2][u] = Ji[r0 + u] * d;
+        const float2 ya = *reinterpret_cast<const float2*>(Ji + c0);
+        const float2 yb = *reinterpret_cast<const float2*>(Ji + c0 + 2);
+        y[r2] = make_float4(ya.x, ya.y, yb.x, yb.y);
+      }
+#pragma unroll
+      for (int r2 = 0; r2 < 2; ++r2)
 #pragma unroll
         for (int u = 0; u < RA; ++u) {
-          const float x = Ji[r0 + u] * d;
-          acc[u][0] = __fmaf_rn(x, y.x, acc[u][0]);
-          acc[u][1] = __fmaf_rn(x, y.y, acc[u][1]);
-          acc[u][2] = __fmaf_rn(x, y.z, acc[u][2]);
-          acc[u][3] = __fmaf_rn(x, y.w, acc[u][3]);
+          acc[u][0] = __fmaf_rn(x[r2][u], y[r2].x, acc[u][0]);
+          acc[u][1] = __fmaf_rn(x[r2][u], y[r2].y, acc[u][1]);
+          acc[u][2] = __fmaf_rn(x[r2][u], y[r2].z, acc[u][2]);
+          acc[u][3] = __fmaf_rn(x[r2][u], y[r2].w, acc[u][3]);
         }
-      }
+    }
+    if (q < n) {
+      const int e = list[q];
+      const int i = kSigned ? (e & 0x7fffffff) : e;
+      const float d = (kSigned && e < 0) ? -Dm[i] : Dm[i];
+      const float* Ji = Jm + i * G::JS;
+      const float2 ya = *reinterpret_cast<const float2*>(Ji + c0);
+      const float2 yb = *reinterpret_cast<const float2*>(Ji + c0 + 2);
+      const float4 y = make_float4(ya.x, ya.y, yb.x, yb.y);
 #pragma unroll
-      for (int u = 0; u < RA; ++u)
+      for (int u = 0; u < RA; ++u) {
+        const float x = Ji[r0 + u] * d;
+        acc[u][0] = __fmaf_rn(x, y.x, acc[u][0]);
+        acc[u][1] = __fmaf_rn(x, y.y, acc[u][1]);
+        acc[u][2] = __fmaf_rn(x, y.z, acc[u][2]);
+        acc[u][3] = __fmaf_rn(x, y.w, acc[u][3]);
+      }
+    }
+  }
+
+  // Full assembly H = M + sum over the active list into dst (rows of stride MS).
+  __device__ __forceinline__ void assemble_full(float* dst) {
+    const float* Mm = Ms();
+    if (lane < G::NABLK) {
+      int r0, c0;
+      assembly_block(r0, c0);
+      float acc[G::RA][4];
+#pragma unroll
+      for (int u = 0; u < G::RA; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+      accumulate_rows<false>(Idx(), nact, r0, c0, acc);
+#pragma unroll
+      for (int u = 0; u < G::RA; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int rr = r0 + u, cc = c0 + v;
-          if (rr < NV && cc <= rr) L[rr * G::MS + cc] = Mm[rr * G::MS + cc] + acc[u][v];
+          if (rr < NV && cc <= rr) dst[rr * G::MS + cc] = Mm[rr * G::MS + cc] + acc[u][v];
         }
     }
     __syncwarp();
-    const bool ok = factor();
-    fmask_bits = act_bits;
-    fmask_valid = true;
-    return ok;
+  }
+
+  // Rows whose side differs between act_bits and hmask_bits, into Chg() (the
+  // top bit marks a row that left the set).  Returns their number (the list
+  // holds the first kChg).
+  __device__ __forceinline__ int changed_rows() {
+    int* chg = Chg();
+    int base = 0;
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+      if (32 * t < m) {
+        const bool on = (act_bits >> t) & 1u;
+        const bool diff = row_valid(t) && (((act_bits ^ hmask_bits) >> t) & 1u);
+        const unsigned bal = __ballot_sync(kFull, diff);
+        const int pos = base + __popc(bal & ((1u << lane) - 1u));
+        if (diff && pos < G::kChg) chg[pos] = (lane + 32 * t) | (on ? 0 : (int)0x80000000);
+        base += __popc(bal);
+      }
+    }
+    __syncwarp();
+    return base;
+  }
+
+  __device__ __forceinline__ bool assemble_and_factor() {
+    if constexpr (kShare) {
+      int nchg = G::kChg + 1;
+      if (__all_sync(kFull, hmask_valid)) nchg = changed_rows();
+      const bool update = nchg <= G::kChg && 4 * nchg <= nact;
+      float* H = Hs();
+      if (update) {
+        if (nchg > 0 && lane < G::NABLK) {
+          int r0, c0;
+          assembly_block(r0, c0);
+          float acc[G::RA][4];
+#pragma unroll
+          for (int u = 0; u < G::RA; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+          accumulate_rows<true>(Chg(), nchg, r0, c0, acc);
+#pragma unroll
+          for (int u = 0; u < G::RA; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const int rr = r0 + u, cc = c0 + v;
+              if (rr < NV && cc <= rr) H[rr * G::MS + cc] += acc[u][v];
+            }
+        }
+        __syncwarp();
+      } else {
+        assemble_full(H);
+      }
+      hmask_bits = act_bits;
+      hmask_valid = true;
+      bool ok = factor(H);
+      if (!ok && update) {
+        assemble_full(H);
+        ok = factor(H);
+      }
+      fmask_bits = act_bits;
+      fmask_valid = true;
+      return ok;
+    } else {
+      assemble_full(Ls());
+      const bool ok = factor();
+      fmask_bits = act_bits;
+      fmask_valid = true;
+      return ok;
+    }
   }
 
   // True when the active set differs from the factored one on any lane.
@@ -629,26 +737,24 @@ struct WarpSolver {
   // ------------------------------------------------- compensated products
   // s[t] + c[t] = J_i . (vh + vl) for the rows of this lane.  The vectors are
   // broadcast slots (16-byte aligned, zero beyond NV); J rows and vectors are
-  // read a quad of columns at a time, and the terms are accumulated in column
+  // read a pair of columns at a time, and the terms are accumulated in column
   // order.
   __device__ __forceinline__ void rows_dot2(const float* vh, const float* vl, float (&s)[MT],
                                             float (&c)[MT]) {
-    const float4* Jm = reinterpret_cast<const float4*>(Js() + lane * G::JS);
-    const float4* vh4 = reinterpret_cast<const float4*>(vh);
-    const float4* vl4 = reinterpret_cast<const float4*>(vl);
+    const float2* Jm = reinterpret_cast<const float2*>(Js() + lane * G::JS);
+    const float2* vh2 = reinterpret_cast<const float2*>(vh);
+    const float2* vl2 = reinterpret_cast<const float2*>(vl);
 #pragma unroll
     for (int t = 0; t < MT; ++t) { s[t] = 0.f; c[t] = 0.f; }
 #pragma unroll 1
-    for (int q = 0; q < G::NQ; ++q) {
-      const float4 xh = vh4[q], xl = vl4[q];
+    for (int q = 0; q < G::NP; ++q) {
+      const float2 xh = vh2[q], xl = vl2[q];
 #pragma unroll
       for (int t = 0; t < MT; ++t)
         if (32 * t < m) {
-          const float4 j = Jm[8 * t * G::JS + q];
+          const float2 j = Jm[16 * t * G::JS + q];
           dot2(s[t], c[t], j.x, xh.x, xl.x);
           dot2(s[t], c[t], j.y, xh.y, xl.y);
-          dot2(s[t], c[t], j.z, xh.z, xl.z);
-          dot2(s[t], c[t], j.w, xh.w, xl.w);
         }
     }
   }
@@ -659,7 +765,7 @@ struct WarpSolver {
   __device__ __forceinline__ void jt_active(const float* v, const float* vlo, float& s,
                                             float& c) {
     const float* Jm = Js();
-    const int* idx = Idx();
+    const idx_t* idx = Idx();
     float s2 = 0.f, c2 = 0.f;
     s = 0.f;
     c = 0.f;
@@ -719,27 +825,25 @@ struct WarpSolver {
 
   // Plain FP32 counterparts, used while the active set is still changing.
   __device__ __forceinline__ void rows_dot(const float* vh, float (&s)[MT]) {
-    const float4* Jm = reinterpret_cast<const float4*>(Js() + lane * G::JS);
-    const float4* v4 = reinterpret_cast<const float4*>(vh);
+    const float2* Jm = reinterpret_cast<const float2*>(Js() + lane * G::JS);
+    const float2* v2 = reinterpret_cast<const float2*>(vh);
 #pragma unroll
     for (int t = 0; t < MT; ++t) s[t] = 0.f;
 #pragma unroll
-    for (int q = 0; q < G::NQ; ++q) {
-      const float4 x = v4[q];
+    for (int q = 0; q < G::NP; ++q) {
+      const float2 x = v2[q];
 #pragma unroll
       for (int t = 0; t < MT; ++t)
         if (32 * t < m) {
-          const float4 j = Jm[8 * t * G::JS + q];
+          const float2 j = Jm[16 * t * G::JS + q];
           s[t] = __fmaf_rn(j.x, x.x, s[t]);
           s[t] = __fmaf_rn(j.y, x.y, s[t]);
-          s[t] = __fmaf_rn(j.z, x.z, s[t]);
-          s[t] = __fmaf_rn(j.w, x.w, s[t]);
         }
     }
   }
   __device__ __forceinline__ float jt_active_plain(const float* v) {
     const float* Jm = Js();
-    const int* idx = Idx();
+    const idx_t* idx = Idx();
     float s = 0.f, s2 = 0.f;
     if (lane < NV) {
       int q = 0;
@@ -802,7 +906,7 @@ struct WarpSolver {
     act_bits = 0;
     float* F = Fs();
     float* Fl = Flo();
-    int* idx = Idx();
+    idx_t* idx = Idx();
     int base = 0;
     float fm = 0.f;
 #pragma unroll
