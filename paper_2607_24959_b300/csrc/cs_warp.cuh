@@ -1486,8 +1486,19 @@ struct WarpSolver {
 
 // One warp per instance; warps claim instances dynamically (counter) or in a
 // static round-robin.
+// Register budget per thread by rows per lane, measured on the quadruped
+// batch (nv 18): each bucket's time alone at budgets 80 / 96 / 112 / 128 was
+// best at 80 for m <= 32 (whose small shared-memory slice lets the most
+// warps in), 96 for m <= 64 and 112 beyond.  The nv 32 kernels, whose
+// shared-memory slices already hold fewer warps per SM, get 32 more so that
+// the 32-wide factor does not spill.  Launches use at most 256 threads.
+__host__ __device__ constexpr int warp_kernel_regs(int NV, int MT) {
+  return (MT <= 1 ? 80 : MT <= 2 ? 96 : MT <= 4 ? 112 : 128) + (NV > 18 ? 32 : 0);
+}
+
 template <int NV, int MT, int MODE>
-__global__ void __launch_bounds__(256) warp_solve_kernel(const __grid_constant__ Params P) {
+__global__ void __maxnreg__(warp_kernel_regs(NV, MT))
+    warp_solve_kernel(const __grid_constant__ Params P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   using G = Geo<NV, MT, true>;
   const int warp = threadIdx.x >> 5;
