@@ -151,6 +151,39 @@ int cs_solve_adjoint(const cs_batch* batch, const cs_options* opt,
                      const float* a, const cs_state* state, const float* g,
                      float* dqfrc, float* daref, float* dJ, void* stream);
 
+/* ---- library-owned adjoint state --------------------------------------- */
+
+/* The same state, allocated and owned by the library: a cs_state whose five
+ * arrays are device memory the library allocated for one batch shape (the
+ * batch's totals and n, and keep_factor: the factor array is allocated only
+ * when it is 1).  It is used with cs_solve_fwd / cs_solve_adjoint like a
+ * caller-built one, and released with cs_state_free.  Creation allocates
+ * device memory (cudaMalloc) and synchronises nothing.  Returns CS_EINVAL for
+ * a NULL or inconsistent argument (out is then NULL), CS_ENOMEM when the
+ * device memory is not available. */
+int cs_state_create(const cs_batch* batch, int32_t keep_factor, cs_state** out);
+
+/* Forward solve into a library-owned state: when *st is NULL a state for
+ * this batch (and opt->keep_factor) is created first and returned in *st;
+ * otherwise *st must be a state from cs_state_create (or from an earlier
+ * call) made for a batch of the same totals and n, and with a factor array
+ * when opt->keep_factor is 1 (CS_EINVAL otherwise).  Then as cs_solve_fwd.
+ * A state this call created is freed again if the launch fails. */
+int cs_solve_fwd_alloc(const cs_batch* batch, const cs_options* opt, float* a,
+                       cs_state** st, void* stream);
+
+/* Copy the per-instance status (CS_ST_*) and Newton step counts of a
+ * library-owned state into caller buffers (device, n entries each; either
+ * may be NULL), asynchronously on `stream`.  They are valid once the forward
+ * that wrote the state and this copy have completed.  CS_EINVAL for a state
+ * that cs_state_create did not make. */
+int cs_state_status(const cs_state* st, int32_t* status, int32_t* iters,
+                    void* stream);
+
+/* Free a library-owned state (after the work that uses it has completed).
+ * NULL, and a pointer that cs_state_create did not return, are ignored. */
+void cs_state_free(cs_state* st);
+
 /* ---- the remaining parameters of Eq. 17: M and D ---------------------- */
 
 /* cs_solve_adjoint that also writes the gradients with respect to M and D
@@ -185,8 +218,9 @@ int cs_solve_fused(const cs_batch* batch, const cs_options* opt,
 
 /* cs_solve_fused with the nonlinear conjugate-gradient forward solver, the
  * other iteration MJX offers for the same objective (Section III-B): search
- * directions preconditioned by M^-1 with the Polak-Ribiere+ beta (restarted
- * when the active set changes and every nv steps) and the exact line search
+ * directions preconditioned by M^-1 with the Polak-Ribiere+ beta (clipped
+ * at zero, and restarted from the preconditioned residual whenever the
+ * conjugated direction is not a descent direction) and the exact line search
  * of Eq. 10; opt->max_iter caps the CG steps (many more than Newton needs).
  * The adjoint is the same IFT rule at the returned point (Eq. 17): it does
  * not depend on the path taken to a* (Eq. 14).  One warp per instance only
@@ -228,10 +262,16 @@ int cs_solve_fused_theta(const cs_batch* batch, const cs_options* opt,
  *
  * Limits and sharing: n above CS_STATIC_MAX_INSTANCES returns
  * CS_EUNSUPPORTED.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and caches it; make that first call before
- * any stream capture.  Every call shares the one array and resets the counter
- * itself; calls whose work overlaps on the GPU (different streams, or
- * different host threads) race on it and must be serialised by the caller. */
+ * address (cudaGetSymbolAddress) and caches it for the life of the process;
+ * make that first call before any stream capture, and do not reset the
+ * device (cudaDeviceReset) after it, which would leave the cached address
+ * stale.  With inst_host != NULL the call uploads the claim order from a
+ * host array that lives only for the call, so it returns CS_EUNSUPPORTED on
+ * a stream that is being captured (index-order claims, inst_host = NULL, do
+ * not upload anything).  Every call shares the one array and resets the
+ * counter itself; calls whose work overlaps on the GPU (different streams,
+ * or different host threads) race on it and must be serialised by the
+ * caller. */
 int cs_solve_fused_static(const cs_batch* batch, const cs_options* opt,
                           const float* g, const cs_inst* inst_host, float* a,
                           float* dqfrc, float* daref, float* dJ,

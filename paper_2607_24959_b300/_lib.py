@@ -101,6 +101,13 @@ _SIGS = {
                                               c_void_p, ctypes.POINTER(CsState), c_void_p,
                                               c_void_p, c_void_p, c_void_p, c_void_p,
                                               c_void_p, c_void_p]),
+    "cs_state_create": (ctypes.c_int, [ctypes.POINTER(CsBatch), c_int32,
+                                       ctypes.POINTER(ctypes.POINTER(CsState))]),
+    "cs_solve_fwd_alloc": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
+                                          c_void_p, ctypes.POINTER(ctypes.POINTER(CsState)),
+                                          c_void_p]),
+    "cs_state_status": (ctypes.c_int, [ctypes.POINTER(CsState), c_void_p, c_void_p, c_void_p]),
+    "cs_state_free": (None, [ctypes.POINTER(CsState)]),
     "cs_fused_workspace_bytes": (c_size_t, [c_int32]),
     "cs_solve_fused_ncg": (ctypes.c_int, [ctypes.POINTER(CsBatch), ctypes.POINTER(CsOptions),
                                           c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

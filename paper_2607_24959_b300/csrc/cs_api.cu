@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <new>
+#include <set>
 
 #include "contact_solve.h"
 #include "cs_host.h"
@@ -231,6 +233,139 @@ int cs_solve_adjoint_theta(const cs_batch* batch, const cs_options* opt, const f
   cudaError_t e = launch_dispatch(csk::MODE_ADJ, batch->nv_max, batch->m_max, P, cfg,
                                   (cudaStream_t)stream, nullptr);
   return e == cudaSuccess ? CS_OK : launch_error(e, "cs_solve_adjoint launch");
+}
+
+// ---- library-owned states ------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+// A state the library allocated: the public struct first (its address is the
+// handle the caller holds), then what the library needs to check and free it.
+struct OwnedState {
+  cs_state pub;
+  int32_t n;
+  int64_t total_M, total_v, total_r;
+  int32_t keep_factor;
+  void* mem;
+};
+
+std::mutex g_owned_mu;
+std::set<const cs_state*> g_owned;
+
+OwnedState* owned(const cs_state* st) {
+  std::lock_guard<std::mutex> lk(g_owned_mu);
+  if (!st || !g_owned.count(st)) return nullptr;
+  return reinterpret_cast<OwnedState*>(const_cast<cs_state*>(st));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+int cs_state_create(const cs_batch* batch, int32_t keep_factor, cs_state** out) {
+  if (!out) return set_error(CS_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  if (!batch) return set_error(CS_EINVAL, "batch must not be NULL");
+  if (batch->n < 0 || batch->total_M < 0 || batch->total_v < 0 || batch->total_r < 0)
+    return set_error(CS_EINVAL, "negative batch size or totals");
+  if (keep_factor != 0 && keep_factor != 1)
+    return set_error(CS_EINVAL, "keep_factor must be 0 or 1");
+  const size_t n = (size_t)batch->n;
+  const size_t b_alo = align256(4 * (size_t)batch->total_v);
+  const size_t b_act = align256((size_t)batch->total_r);
+  const size_t b_L = keep_factor ? align256(4 * (size_t)batch->total_M) : 0;
+  const size_t b_st = align256(4 * n);
+  const size_t total = b_alo + b_act + b_L + 2 * b_st;
+  OwnedState* o = new (std::nothrow) OwnedState();
+  if (!o) return set_error(CS_ENOMEM, "state: host allocation failed");
+  o->n = batch->n;
+  o->total_M = batch->total_M;
+  o->total_v = batch->total_v;
+  o->total_r = batch->total_r;
+  o->keep_factor = keep_factor;
+  o->mem = nullptr;
+  if (total > 0) {
+    cudaError_t e = cudaMalloc(&o->mem, total);
+    if (e != cudaSuccess) {
+      delete o;
+      return set_error(CS_ENOMEM, "state: %s", cudaGetErrorString(e));
+    }
+  }
+  char* cur = (char*)o->mem;
+  o->pub.a_lo = (float*)cur;
+  cur += b_alo;
+  o->pub.act = (uint8_t*)cur;
+  cur += b_act;
+  o->pub.L = keep_factor ? (float*)cur : nullptr;
+  cur += b_L;
+  o->pub.status = (int32_t*)cur;
+  cur += b_st;
+  o->pub.iters = (int32_t*)cur;
+  {
+    std::lock_guard<std::mutex> lk(g_owned_mu);
+    g_owned.insert(&o->pub);
+  }
+  *out = &o->pub;
+  return CS_OK;
+}
+
+void cs_state_free(cs_state* st) {
+  OwnedState* o = owned(st);
+  if (!o) return;
+  {
+    std::lock_guard<std::mutex> lk(g_owned_mu);
+    g_owned.erase(st);
+  }
+  if (o->mem) cudaFree(o->mem);
+  delete o;
+}
+
+int cs_solve_fwd_alloc(const cs_batch* batch, const cs_options* opt, float* a, cs_state** st,
+                       void* stream) {
+  if (!st) return set_error(CS_EINVAL, "st must not be NULL");
+  int rc = check_batch(batch, opt);
+  if (rc != CS_OK) return rc;
+  bool created = false;
+  if (!*st) {
+    rc = cs_state_create(batch, opt->keep_factor ? 1 : 0, st);
+    if (rc != CS_OK) return rc;
+    created = true;
+  } else {
+    const OwnedState* o = owned(*st);
+    if (!o) return set_error(CS_EINVAL, "*st is not a state made by cs_state_create");
+    if (o->n != batch->n || o->total_M != batch->total_M || o->total_v != batch->total_v ||
+        o->total_r != batch->total_r)
+      return set_error(CS_EINVAL, "the state was made for a batch of other sizes");
+    if (opt->keep_factor && !o->keep_factor)
+      return set_error(CS_EINVAL, "keep_factor is 1 but the state has no factor array");
+  }
+  rc = cs_solve_fwd(batch, opt, a, *st, stream);
+  if (rc != CS_OK && created) {
+    cs_state_free(*st);
+    *st = nullptr;
+  }
+  return rc;
+}
+
+int cs_state_status(const cs_state* st, int32_t* status, int32_t* iters, void* stream) {
+  const OwnedState* o = owned(st);
+  if (!o) return set_error(CS_EINVAL, "not a state made by cs_state_create");
+  if (o->n == 0) return CS_OK;
+  const size_t bytes = 4 * (size_t)o->n;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (status) {
+    cudaError_t e = cudaMemcpyAsync(status, o->pub.status, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "cs_state_status");
+  }
+  if (iters) {
+    cudaError_t e = cudaMemcpyAsync(iters, o->pub.iters, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "cs_state_status");
+  }
+  return CS_OK;
 }
 
 size_t cs_fused_workspace_bytes(int32_t n) {

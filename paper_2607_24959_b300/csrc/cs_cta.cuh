@@ -11,9 +11,11 @@
 //    memory;
 //  * H = M + J_act^T D J_act: 4x4 register blocks of the lower triangle,
 //    split over groups of active rows when there are few blocks;
-//  * Cholesky: right-looking in shared memory (column scale, then the
-//    trailing update spread over all threads);
-//  * triangular solves: one warp, rows spread over its lanes, shuffles.
+//  * Cholesky: blocked right-looking in shared memory over 32-column panels
+//    (warp 0 factors the diagonal block, all threads solve the panel below
+//    it and update the trailing matrix; see factor());
+//  * triangular solves: blocked the same way (warp 0 on each 32 x 32
+//    diagonal block, all threads on the rectangular block beside it).
 #pragma once
 
 #include "cs_warp.cuh"

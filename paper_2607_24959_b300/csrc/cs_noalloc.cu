@@ -73,6 +73,15 @@ extern "C" int cs_solve_fused_static(const cs_batch* batch, const cs_options* op
   int32_t* order = scratch + kCounterWords;
   cudaStream_t s = (cudaStream_t)stream;
   if (inst_host) {
+    // the claim order is uploaded from a host vector that lives only for the
+    // call: a stream being captured would record a copy from freed memory
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess) return cuda_error(ce, "cs_solve_fused_static: cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+      return set_error(CS_EUNSUPPORTED,
+                       "cs_solve_fused_static: cost-ordered claims (inst_host != NULL) upload "
+                       "a host array and cannot be captured; pass inst_host = NULL");
     // most expensive instances are claimed first (m nv^2 + nv^3)
     std::vector<std::pair<double, int32_t>> cost(batch->n);
     for (int32_t i = 0; i < batch->n; ++i) {

@@ -150,6 +150,59 @@ def solve_fwd(batch: DeviceBatch, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
     return a, state
 
 
+class OwnedState:
+    """A forward state allocated and owned by the library (cs_solve_fwd_alloc /
+    cs_state_create); usable wherever a State is, freed by close()."""
+
+    def __init__(self, ptr, n: int, device):
+        self._ptr = ptr
+        self.n = n
+        self.device = device
+        self.keep_factor = bool(ptr.contents.L)
+
+    def cstruct(self) -> _lib.CsState:
+        return self._ptr.contents
+
+    def status_iters(self):
+        """Per-instance status and Newton step counts (cs_state_status)."""
+        st = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.device)
+        it = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.device)
+        _lib.check(_lib.load().cs_state_status(self._ptr, _ptr(st), _ptr(it), _stream()),
+                   "cs_state_status")
+        return st[:self.n], it[:self.n]
+
+    def close(self):
+        if self._ptr:
+            torch.cuda.synchronize(self.device)
+            _lib.load().cs_state_free(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_fwd_owned(batch: DeviceBatch, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER,
+                    keep_factor=True, warps_per_block=0, a=None, state: OwnedState | None = None):
+    """Forward solve into a library-owned state (cs_solve_fwd_alloc); returns
+    (a, OwnedState).  A state from an earlier call on a batch of the same
+    sizes is reused when given."""
+    lib = _lib.load()
+    dev = batch.M.device
+    if a is None:
+        a = torch.empty(max(batch.total_v, 1), dtype=torch.float32, device=dev)
+    b = batch.cstruct()
+    o = options(tol, max_iter, keep_factor, warps_per_block)
+    ptr = state._ptr if state is not None else ctypes.POINTER(_lib.CsState)()
+    _lib.check(lib.cs_solve_fwd_alloc(ctypes.byref(b), ctypes.byref(o), _ptr(a),
+                                      ctypes.byref(ptr), _stream()), "cs_solve_fwd_alloc")
+    if state is None:
+        state = OwnedState(ptr, batch.n, dev)
+    return a, state
+
+
 def solve_adjoint(batch: DeviceBatch, a, state: State, g, tol=DEFAULT_TOL,
                   max_iter=DEFAULT_MAX_ITER, warps_per_block=0, out=None, theta=False):
     """IFT adjoint at the forward state; returns (dqfrc, daref, dJ), or with

@@ -129,3 +129,38 @@ def test_serve_argument_checks_without_gpu(lib):
     t = ctypes.c_uint64(0)
     assert lib.cs_serve_submit(None, None, ctypes.byref(t)) == _lib.CS_EINVAL
     assert lib.cs_serve_poll(None, 1, None) == _lib.CS_EINVAL
+
+
+def test_library_owned_state_without_gpu(lib):
+    """The library-owned form of the adjoint state (cs_state_create,
+    cs_solve_fwd_alloc, cs_state_status, cs_state_free): argument checks on
+    the host, and the whole life cycle of an empty state, which needs no
+    device memory."""
+    P = ctypes.POINTER(_lib.CsState)
+    st = P()
+    b = _batch()
+    assert lib.cs_state_create(ctypes.byref(b), 1, None) == _lib.CS_EINVAL
+    assert lib.cs_state_create(None, 1, ctypes.byref(st)) == _lib.CS_EINVAL
+    assert not st
+    assert lib.cs_state_create(ctypes.byref(_batch(n=-1)), 1, ctypes.byref(st)) == _lib.CS_EINVAL
+    assert lib.cs_state_create(ctypes.byref(b), 2, ctypes.byref(st)) == _lib.CS_EINVAL
+    # a caller-built cs_state is not a library-owned one
+    mine = _lib.CsState()
+    assert lib.cs_state_status(ctypes.byref(mine), None, None, None) == _lib.CS_EINVAL
+    assert b"cs_state_create" in lib.cs_last_error()
+    lib.cs_state_free(ctypes.cast(ctypes.byref(mine), P))     # ignored
+    lib.cs_state_free(None)                                   # ignored
+    o = _opts()
+    assert lib.cs_solve_fwd_alloc(ctypes.byref(b), ctypes.byref(o), None, None,
+                                  None) == _lib.CS_EINVAL
+    other = ctypes.cast(ctypes.byref(mine), P)
+    assert lib.cs_solve_fwd_alloc(ctypes.byref(b), ctypes.byref(o), 0x30000, ctypes.byref(other),
+                                  None) == _lib.CS_EINVAL
+    # an empty batch: the state owns no device memory
+    e = _batch(n=0, total_M=0, total_J=0, total_v=0, total_r=0)
+    assert lib.cs_state_create(ctypes.byref(e), 0, ctypes.byref(st)) == _lib.CS_OK
+    assert st and not st.contents.L
+    assert lib.cs_state_status(st, None, None, None) == _lib.CS_OK
+    lib.cs_state_free(st)
+    # after cs_state_free the pointer is no longer a state of the library
+    assert lib.cs_state_status(st, None, None, None) == _lib.CS_EINVAL

@@ -36,16 +36,34 @@ def _close(w, got, ref):
             assert parity.rel(got["dJ"][oJ:oJ + m * nv], ref["dJ"][oJ:oJ + m * nv]) <= parity.G_TOL
 
 
+def _batch_with_cta_instances():
+    """Quadruped instances (one warp each) and nv = 96 instances (one CTA
+    each, as in the scaling-extremes workload) in one batch."""
+    parts = [W.quadruped(n=400, seed=99).instance(b) for b in range(400)]
+    big = W.generate("nv96-mix", 12, 96, 16, seed=98, cond=1e4)
+    parts += [big.instance(b) for b in range(big.n)]
+    return W.pack(parts, name="warp+cta")
+
+
 @pytest.mark.gpu
-def test_static_scratch_matches_workspace_path_twice(cuda_device):
-    w = W.quadruped(n=2500, seed=99)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_static_scratch_matches_workspace_path_twice(cuda_device, mixed):
+    w = _batch_with_cta_instances() if mixed else W.quadruped(n=2500, seed=99)
     batch = solver.DeviceBatch.from_workload(w, cuda_device)
     g = torch.from_numpy(w.g).to(cuda_device)
     ref = _outputs(solver.solve_fused(batch, g))
+    out = solver.alloc_fused(batch)          # outputs preallocated by the caller
+    # the first call in a fresh process may load the library's module that
+    # holds the static array (the runtime's lazy module loading), which is
+    # where the array's memory comes from; it is checked like the others
+    _close(w, _outputs(solver.solve_fused_static(batch, g, out=out)), ref)
+    free0 = torch.cuda.mem_get_info(cuda_device)[0]
     # two calls in a row: cost-ordered claims, then index-order claims that
     # reuse the counter and order left in the static array by the first call
     for ordered in (True, False):
-        got = _outputs(solver.solve_fused_static(batch, g, cost_ordered=ordered))
+        got = _outputs(solver.solve_fused_static(batch, g, cost_ordered=ordered, out=out))
+        # the calls allocate no device memory
+        assert torch.cuda.mem_get_info(cuda_device)[0] == free0
         _close(w, got, ref)
 
 
