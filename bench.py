@@ -218,7 +218,8 @@ def cpu_baseline(w, max_instances=None, threads=None, single_sample=2048, repeat
             ts.append(time.perf_counter() - t0)
         return statistics.median(ts)
 
-    dt = timed(oracle.PreparedWorkload(ws), threads)
+    pw = oracle.PreparedWorkload(ws)
+    dt = timed(pw, threads)
     res = {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
            "sample": f"first {n} of the {w.n} instances, forward + adjoint, "
                      f"{threads} threads, median of {repeats} passes of {dt:.3f} s wall"}
@@ -230,6 +231,7 @@ def cpu_baseline(w, max_instances=None, threads=None, single_sample=2048, repeat
                                 "sample": f"first {n1} instances, one thread, median of "
                                           f"{repeats} passes of {d1:.3f} s wall"}
     res["build"] = "gcc -O3 -march=native -std=c99 -ffp-contract=off"
+    res["iters_mean"] = float(pw.iters.mean()) if n else 0.0
     return res
 
 
@@ -521,6 +523,11 @@ def run_gpu(args):
             "iters_mean": float(iters.mean()), "iters_max": int(iters.max())}
     if e2e:
         line["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, max_instances=args.cpu_sample)
+        line["oracle_iters_mean"] = line["cpu_baseline"].pop("iters_mean", None)
+    if args.configs and world == 1:
+        line["configs"] = run_configs(args, peaks, peak_src)
     if not args.no_serve and world == 1:
         del plan, out, batch
         torch.cuda.empty_cache()
@@ -531,11 +538,81 @@ def run_gpu(args):
         line["elliptic"] = run_elliptic(args)
     if not args.no_ncg and world == 1:
         line["ncg"] = run_ncg(args)
-    if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(w, max_instances=args.cpu_sample)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_configs(args, peaks, peak_src):
+    """The other configurations of the benchmark suite, each on its own: the
+    fused forward + adjoint through a plan (bucketed, autotuned, one CUDA
+    graph), CUDA-event timed on the plan's stream after warm-up, with the same
+    roofline accounting and an oracle baseline on the host cores."""
+    import torch
+    from paper_2607_24959_b300 import solver
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    legs = {}
+    for name in args.configs.split(","):
+        if not name:
+            continue
+        w = make_workload(name, 0)
+        batch = solver.DeviceBatch.from_workload(w, dev)
+        g = torch.from_numpy(w.g).to(dev)
+        out = solver.alloc_fused(batch)
+        stream = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(stream):
+            plan = solver.FusedPlan(batch, g, tol=args.tol, max_iter=args.max_iter,
+                                    autotune=True, graph=True, out=out)
+            t_w = time.monotonic()
+            n_w = 0
+            while n_w < 3 or time.monotonic() - t_w < 0.2:
+                plan.launch()
+                n_w += 1
+            steps = max(5, min(args.steps, 100))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                plan.launch()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        st = out.status.cpu().numpy()[:w.n]
+        it = out.iters.cpu().numpy()[:w.n]
+        daref = out.daref.cpu().numpy()
+        act = np.array([np.count_nonzero(daref[o:o + mm]) for o, mm in
+                        zip(w.inst["off_r"], w.inst["m"])])
+        flops, byts = algorithmic_work(w.inst, it, act)
+        t_s = ms / 1e3
+        frac_alu = flops / t_s / 1e12 / fp32_peak
+        frac_hbm = byts / t_s / 1e9 / hbm_peak
+        info = plan.describe()
+        plan.close()
+        legs[name] = {
+            "metric": "fwd+IFT-adjoint contact solves/s", "value": w.n / t_s, "unit": UNIT,
+            "ms_per_step": ms, "steps": steps, "config": workload_config(name, w),
+            "roofline": {"bound": "alu" if frac_alu >= frac_hbm else "hbm",
+                         "achieved": flops / t_s / 1e12 if frac_alu >= frac_hbm
+                         else byts / t_s / 1e9,
+                         "peak": fp32_peak if frac_alu >= frac_hbm else hbm_peak,
+                         "unit": "TFLOP/s" if frac_alu >= frac_hbm else "GB/s",
+                         "frac": max(frac_alu, frac_hbm), "traffic": None,
+                         "hbm_frac": frac_hbm, "alu_frac": frac_alu,
+                         "algorithmic_flops_per_launch": flops,
+                         "algorithmic_bytes_per_launch": byts},
+            "plan": info, "status_counts": np.bincount(st, minlength=6).tolist(),
+            "iters_mean": float(it.mean()), "iters_max": int(it.max()),
+            "gpu_launches_per_step": info["kernels"]}
+        if not args.no_cpu_baseline:
+            cb = cpu_baseline(w, repeats=3)
+            legs[name]["cpu_baseline"] = cb
+        del out, batch, g
+        torch.cuda.empty_cache()
+    return legs
 
 
 def run_memory(args):
@@ -775,6 +852,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=32768)
+    ap.add_argument("--configs", default="tiny,franka,nv96,nc256",
+                    help="comma-separated workloads measured beside the headline one "
+                         "(empty to skip)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-ncg", action="store_true",
                     help="skip the conjugate-gradient forward solver leg")

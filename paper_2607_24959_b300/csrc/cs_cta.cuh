@@ -197,111 +197,104 @@ struct CtaSolver {
   // ------------------------------------------------------------- Cholesky
   // Blocked right-looking Cholesky, in place on the lower rows of Ls() (the
   // padded rows are identity), panels of 32 columns:
-  //  1. the diagonal block by warp 0, left-looking (lane l = row kb + l),
-  //     four columns per round: each lane forms its row's four partial dot
-  //     products in one pass, the 4 x 4 diagonal block is gathered by
-  //     shuffles and factored by every lane, one warp barrier pair per round;
-  //  2. the rows below it by forward substitution against that block, four
-  //     threads per row splitting each inner product;
+  //  1. the 32 x 32 diagonal block by warp 0 with the block in registers
+  //     (lane l holds row kb + l; right-looking over the block's columns, the
+  //     pivot broadcast by a shuffle and each column's entries by shuffles,
+  //     the next pivot's update taken off the shuffle chain), as the warp
+  //     solver factors its whole matrix; a narrower last panel is padded
+  //     with identity rows and columns inside the registers;
+  //  2. the rows below it by all warps, four rows at a time per warp with a
+  //     row's panel entries spread over the lanes: forward substitution
+  //     against the diagonal block column by column (L_ic = x_c / L_cc,
+  //     broadcast by a shuffle, then x_j -= L_ic L_jc on the lanes j > c);
   //  3. the trailing matrix updated by all threads in 2x2 register blocks.
   // Three barriers per panel.  Returns false on a non-positive pivot.
+  //
+  // Measured on the nv96 workload (clock64 per phase, two CTAs per SM): the
+  // left-looking diagonal block with four-column rounds took about 9.6 k
+  // cycles per block, the register one 5.7 k; the panel solve with four
+  // threads per row and a warp barrier per column about 12.5 k per panel,
+  // one thread per row (two warps busy) 14.8 k.
+  //
+  // Both helpers are static (every operand passed explicitly): a non-inlined
+  // member function would take the solver object by address and move it to
+  // local memory for the whole kernel.
+  __device__ static __noinline__ bool factor_diag_block(float* L, float* dv, int MS, int lane,
+                                                        int kb, int bs) {
+    float* Lr = L + (kb + min(lane, bs - 1)) * MS + kb;
+    float h[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const bool real = lane < bs && c <= lane;
+      h[c] = real ? Lr[c] : (c == lane ? 1.f : 0.f);
+    }
+    float diag = 1.f, piv = h[0];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const float d = __shfl_sync(kFull, piv, k);
+      const float rs = rsqrtf(d);
+      const float lkk = d * rs;
+      const float l = (lane == k) ? lkk : h[k] * rs;
+      h[k] = l;
+      diag = (lane == k) ? lkk : diag;
+      if (k + 1 < 32) piv = __fmaf_rn(-l, l, h[k + 1]);
+#pragma unroll
+      for (int c = k + 1; c < 32; ++c) h[c] = __fmaf_rn(-l, __shfl_sync(kFull, l, c), h[c]);
+    }
+    if (lane < bs) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c <= lane) Lr[c] = h[c];
+      dv[kb + lane] = 1.0f / diag;
+    }
+    return !__any_sync(kFull, lane < bs && !(diag > 0.f && diag < CUDART_INF_F));
+  }
+
+  // Rows [r0, nc) of the full panel kb (32 columns): L_i = H_i L_kk^-T.  Each
+  // warp takes every eighth row, four rows at a time, with a row's 32 panel
+  // entries spread over the lanes (lane c holds column c); column by column
+  // the lane that owns column c scales it by the reciprocal pivot and
+  // broadcasts it, and the lanes after it subtract its multiple of the
+  // diagonal block's column c, which each lane reads once per column for
+  // all four rows.
+  __device__ static __noinline__ void panel_solve(float* L, const float* dv, int MS, int lane,
+                                                  int warp, int kb, int r0, int nc) {
+    const float dl = dv[kb + lane];
+    const float* Lk = L + kb * MS + kb + lane * MS;  // row kb + lane of the block
+#pragma unroll 1
+    for (int i0 = r0 + 4 * warp; i0 < nc; i0 += 4 * kCtaWarps) {
+      float x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = (i0 + u < nc) ? L[(i0 + u) * MS + kb + lane] : 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float lj = (lane > c) ? Lk[c] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float y = __shfl_sync(kFull, x[u] * dl, c);
+          x[u] = (lane == c) ? y : __fmaf_rn(-y, lj, x[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u < nc) L[(i0 + u) * MS + kb + lane] = x[u];
+    }
+  }
+
   __device__ __forceinline__ bool factor() {
     float* L = Ls();
-    float* dv = V(C_DINV);
     const int nc = geo.nvcap, MS = geo.MS;
     bool ok = true;
 #pragma unroll 1
     for (int kb = 0; kb < nc; kb += 32) {
       const int bs = min(32, nc - kb);
       if (warp == 0) {
-        const int row = kb + min(lane, bs - 1);
-        float* Lr = L + row * MS + kb;
-#pragma unroll 1
-        for (int cb = 0; cb < bs; cb += 4) {  // bs is a multiple of 4
-          const float* Lb = L + (kb + cb) * MS + kb;
-          float acc[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) acc[u] = Lr[cb + u];
-#pragma unroll 1
-          for (int i = 0; i < cb; i += 4) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              const float x = Lr[i + v];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) acc[u] = __fmaf_rn(-x, Lb[u * MS + i + v], acc[u]);
-            }
-          }
-          float blk[4][4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int w = 0; w <= u; ++w) blk[u][w] = __shfl_sync(kFull, acc[w], cb + u);
-          float rs[4], lkk[4];
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            float d = blk[w][w];
-#pragma unroll
-            for (int v = 0; v < w; ++v) d = __fmaf_rn(-blk[w][v], blk[w][v], d);
-            ok = ok && (d > 0.f) && (d < CUDART_INF_F);
-            rs[w] = rsqrtf(d);
-            lkk[w] = d * rs[w];
-#pragma unroll
-            for (int u = w + 1; u < 4; ++u) {
-              float e = blk[u][w];
-#pragma unroll
-              for (int v = 0; v < w; ++v) e = __fmaf_rn(-blk[u][v], blk[w][v], e);
-              blk[u][w] = e * rs[w];
-            }
-            blk[w][w] = lkk[w];
-          }
-          float out[4];
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            float e = acc[w];
-#pragma unroll
-            for (int v = 0; v < w; ++v) e = __fmaf_rn(-out[v], blk[w][v], e);
-            out[w] = e * rs[w];
-          }
-          __syncwarp();
-          if (lane >= cb + 4 && lane < bs) {
-#pragma unroll
-            for (int w = 0; w < 4; ++w) Lr[cb + w] = out[w];
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (lane == cb + u) {
-#pragma unroll
-              for (int w = 0; w <= u; ++w) Lr[cb + w] = blk[u][w];
-              dv[kb + cb + u] = 1.0f / lkk[u];
-            }
-          }
-          __syncwarp();
-        }
+        ok = factor_diag_block(L, V(C_DINV), MS, lane, kb, bs) && ok;
         if (lane == 0) Red()[4 * kCtaWarps + 7] = ok ? 1.f : 0.f;
       }
       __syncthreads();
       const int r0 = kb + bs, nrows = nc - r0;
-      if (nrows > 0) {
-        const int q = tid & 3;
-#pragma unroll 1
-        for (int base = 0; base < nrows; base += kCtaThreads / 4) {
-          const int r = base + (tid >> 2);
-          const bool active = r < nrows;
-          const int i = r0 + min(r, nrows - 1);
-          float* Li = L + i * MS + kb;
-#pragma unroll 1
-          for (int c = 0; c < bs; ++c) {
-            const float* Lc = L + (kb + c) * MS + kb;
-            float part = 0.f;
-#pragma unroll 1
-            for (int pp = q; pp < c; pp += 4) part = __fmaf_rn(Li[pp], Lc[pp], part);
-            part += __shfl_xor_sync(kFull, part, 1);
-            part += __shfl_xor_sync(kFull, part, 2);
-            if (active && q == 0) Li[c] = (Li[c] - part) * dv[kb + c];
-            __syncwarp();
-          }
-        }
-      }
+      if (nrows > 0) panel_solve(L, V(C_DINV), MS, lane, warp, kb, r0, nc);
       __syncthreads();
       if (nrows > 0) {
         const int nb2 = (nrows + 1) >> 1;
@@ -780,6 +773,27 @@ struct CtaSolver {
   }
 
   // ------------------------------------------------------------- forward
+  // Whether the correction z (shared slot, nvcap entries) would move a by at
+  // most kStepTol max|a| and every active force D_i (J z)_i by at most
+  // kForceTol fmax (fmax from the last compensated residual).  All threads.
+  __device__ __forceinline__ bool small_correction(const float* z) {
+    float zm = 0.f, am = 0.f;
+    if (tid < nv) {
+      zm = fabsf(z[tid]);
+      am = fabsf(V(C_AH)[tid]);
+    }
+    const float zmax = block_max(zm);
+    const float amax = block_max(am);
+    if (!(zmax <= kStepTol * amax)) return false;
+    float s[MTC], c[MTC];
+    rows_dot(z, z, false, s, c);
+    float df = 0.f;
+#pragma unroll
+    for (int u = 0; u < MTC; ++u)
+      if ((act_bits >> u) & 1u) df = fmaxf(df, fabsf(D_r[u] * s[u]));
+    return block_max(df) <= kForceTol * fmax;
+  }
+
   __device__ __forceinline__ int forward(const Params& P, int* iters) {
     *iters = 0;
     if (!factor_M()) return CS_ST_CHOLFAIL;
@@ -811,7 +825,6 @@ struct CtaSolver {
       }
       if (rmax <= P.tol * scale) return CS_ST_OK;
       const bool same = !block_any(act_bits != prev_bits);
-      if (k > 0 && same && prev_small) return CS_ST_OK;
       if (k >= P.max_iter) return CS_ST_MAXITER;
       cg = cg && same;
       if (need_refactor()) {
@@ -822,6 +835,12 @@ struct CtaSolver {
       for (int j = tid; j < geo.nvcap; j += kCtaThreads) p[j] = V(C_R)[j];
       __syncthreads();
       chol_solve(C_P);
+      // Once the active set has settled (compensated phase, the same set as
+      // at the previous point), the FP32 Newton correction z estimates the
+      // remaining error of a: a is returned as it is when z would move it by
+      // <= kStepTol |a| and every active force by <= kForceTol |f|, or when
+      // the step just taken was that small (as in the warp solver)
+      if (precise && k > 0 && same && (prev_small || small_correction(p))) return CS_ST_OK;
       float zr = 0.f, ptr = 0.f;
       if (tid < nv) zr = p[tid] * V(C_R)[tid];
       float d0 = 0.f;
@@ -883,10 +902,6 @@ struct CtaSolver {
     __syncthreads();
     chol_solve(C_WH);
     float* Lm = Lam();
-    float lam_prev[MTC];
-#pragma unroll
-    for (int u = 0; u < MTC; ++u) lam_prev[u] = 0.f;
-    float dmax_prev = CUDART_INF_F;
     const float* Jm = Js();
     const float* Mm = Ms();
     const int* idx = Idx();
@@ -895,7 +910,7 @@ struct CtaSolver {
     for (int it = 0; it <= kAdjointRefineMax; ++it) {
       float s[MTC], c[MTC];
       rows_dot(wh, wl, true, s, c);
-      float lmax = 0.f, dl = 0.f;
+      float lmax = 0.f;
 #pragma unroll
       for (int u = 0; u < MTC; ++u) {
         if (kCtaThreads * u < m) {
@@ -909,18 +924,10 @@ struct CtaSolver {
             Lamlo()[row(u)] = lamlo;
           }
           lmax = fmaxf(lmax, fabsf(lam));
-          dl = fmaxf(dl, fabsf(lam - lam_prev[u]));
-          lam_prev[u] = lam;
         }
       }
       lmax = block_max(lmax);
-      dl = block_max(dl);
-      float wm = 0.f;
-      if (tid < nv) wm = fabsf(wh[tid]);
-      const float wmax = block_max(wm);
-      if (it > 0 && ((dmax_prev <= kStepTol * wmax && dl <= kForceTol * lmax) ||
-                     it == kAdjointRefineMax))
-        break;
+      if (it == kAdjointRefineMax) break;
       float* js_s = V(C_X);
       float* js_c = V(C_MP);
       const float* Lml = Lamlo();
@@ -953,16 +960,32 @@ struct CtaSolver {
       for (int j = tid; j < geo.nvcap; j += kCtaThreads) rho[j] = (j < nv) ? rv : 0.f;
       __syncthreads();
       chol_solve(C_R);
-      float dm = 0.f;
+      // the correction's size, in w and in the active lambda = D (J dw): when
+      // both are below the adjoint's resolution (kAdjStepTol, kAdjForceTol,
+      // as in the warp solver) w is kept, and lambda already belongs to it
+      float dm = 0.f, wm = 0.f;
       if (tid < nv) {
-        const float dw = rho[tid];
+        dm = fabsf(rho[tid]);
+        wm = fabsf(wh[tid]);
+      }
+      const float dmax = block_max(dm);
+      const float wmax = block_max(wm);
+      if (dmax <= kAdjStepTol * wmax) {
+        float sd[MTC], cd[MTC];
+        rows_dot(rho, rho, false, sd, cd);
+        float dl = 0.f;
+#pragma unroll
+        for (int u = 0; u < MTC; ++u)
+          if ((act_bits >> u) & 1u) dl = fmaxf(dl, fabsf(D_r[u] * sd[u]));
+        if (block_max(dl) <= kAdjForceTol * lmax) break;
+      }
+      if (tid < nv) {
         float hh = wh[tid], ll = wl[tid];
-        WarpSolver<1, 1>::add_to_pair(hh, ll, dw);
+        WarpSolver<1, 1>::add_to_pair(hh, ll, rho[tid]);
         wh[tid] = hh;
         wl[tid] = ll;
-        dm = fabsf(dw);
       }
-      dmax_prev = block_max(dm);
+      __syncthreads();
     }
     __syncthreads();
   }
