@@ -339,13 +339,31 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
 
 def run_serve(args):
     """Serving stream (Poisson arrivals, nv in {3,9,18,96}, nc in 0..64):
-    continuous batching next to fixed-size launches of the same requests."""
+    continuous batching next to fixed-size launches of the same requests; then
+    a sweep of the arrival rate (the same mix, fewer requests per rate above
+    the headline one) to find where each policy stops keeping up."""
     t_arr, reqs = _serve_pool(args.serve_requests, args.serve_rate, 1005)
     cont = serve_run(t_arr, reqs, "continuous")
     fixed = serve_run(t_arr, reqs, "fixed", fixed_batch=args.serve_fixed_batch)
-    return {"requests": args.serve_requests, "rate_per_s": args.serve_rate,
-            "mix": "nv {3,9,18,96} p {.3,.3,.3,.1}, nc U{0..64}, fwd + adjoint each",
-            "continuous": cont, f"fixed_{args.serve_fixed_batch}": fixed}
+    out = {"requests": args.serve_requests, "rate_per_s": args.serve_rate,
+           "mix": "nv {3,9,18,96} p {.3,.3,.3,.1}, nc U{0..64}, fwd + adjoint each",
+           "continuous": cont, f"fixed_{args.serve_fixed_batch}": fixed}
+    sweep = []
+    for rate in [float(r) for r in args.serve_sweep.split(",") if r]:
+        n = int(min(args.serve_requests, max(20000, rate * 0.4)))
+        t_s, r_s = _serve_pool(n, rate, 1005)
+        row = {"rate_per_s": rate, "requests": n}
+        for pol in ("continuous", "fixed"):
+            res = serve_run(t_s, r_s, pol, fixed_batch=args.serve_fixed_batch)
+            row[pol] = {k: res[k] for k in ("p50_ms", "p99_ms", "solves_per_s", "ok",
+                                            "mean_batch", "max_inflight")}
+        sweep.append(row)
+    if sweep:
+        out["rate_sweep"] = sweep
+        out["rate_sweep_note"] = ("each row is its own stream of Poisson arrivals at that rate; "
+                                  "a policy keeps up while solves_per_s matches the rate, and its "
+                                  "latency grows without bound past that knee")
+    return out
 
 
 def run_reference(args):
@@ -870,6 +888,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200000)
     ap.add_argument("--serve-rate", type=float, default=50000.0)
     ap.add_argument("--serve-fixed-batch", type=int, default=1024)
+    ap.add_argument("--serve-sweep", default="200000,500000,1000000",
+                    help="arrival rates (req/s) of the serving sweep; empty to skip")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -75,6 +75,9 @@ extern "C" {
 #define CS_ST_FAILED 6     /* serving: the request's batch failed to launch
                               or transfer (the error is counted in
                               cs_serve_stats.failed_launches) */
+#define CS_ST_TIMEOUT 7    /* serving: the request waited in the queue longer
+                              than cs_serve_config.queue_timeout_ms and was
+                              not run (counted in cs_serve_stats.timed_out) */
 
 /* One instance of a ragged batch (40 bytes).  Offsets are in elements. */
 typedef struct cs_inst {
@@ -428,7 +431,9 @@ typedef struct cs_serve_config {
   float tol;
   int32_t max_iter;
   int32_t max_queue;
-  int32_t reserved;
+  int32_t queue_timeout_ms; /* > 0: a request still queued (not yet admitted
+                               to a batch) this long after its submission is
+                               completed with CS_ST_TIMEOUT; 0 = no limit */
 } cs_serve_config;
 
 /* One request: a forward solve followed by the IFT adjoint for g.  All
@@ -452,7 +457,8 @@ typedef struct cs_result {
 typedef struct cs_serve_stats {
   int64_t submitted, completed, batches, batched_requests, queued;
   int32_t max_inflight;    /* most batches on the GPU at once */
-  int32_t failed_launches;
+  int32_t failed_launches; /* batches whose copy, launch or completion failed */
+  int64_t timed_out;       /* requests completed with CS_ST_TIMEOUT */
 } cs_serve_stats;
 
 typedef struct cs_server cs_server; /* opaque, owned by the library */
@@ -492,6 +498,23 @@ int cs_serve_get_stats(cs_server* srv, cs_serve_stats* stats);
 
 /* Stop admitting, wait for the batches in flight, free everything. */
 void cs_serve_destroy(cs_server* srv);
+
+/* Host-side fault injection, for testing how a server handles failures
+ * without making the device fail.  Before each step of a batch the
+ * scheduler calls hook(stage, batch, user), batch numbering the batches in
+ * the order they are launched from 0; a nonzero return makes that step fail
+ * as if the runtime call had failed (the step is not issued), so the batch's
+ * requests complete with CS_ST_FAILED, cs_serve_stats.failed_launches counts
+ * it, and its slot is reused.  Stages: */
+#define CS_SERVE_FAULT_H2D 0      /* the batch's input copy */
+#define CS_SERVE_FAULT_LAUNCH 1   /* each bucket kernel launch */
+#define CS_SERVE_FAULT_D2H 2      /* the batch's output copy */
+#define CS_SERVE_FAULT_COMPLETE 3 /* the completion the event reports */
+typedef int (*cs_serve_fault_fn)(int stage, int64_t batch, void* user);
+
+/* Install (or, with NULL, remove) the hook.  It is called from the
+ * scheduler's thread and must not call back into the server. */
+int cs_serve_set_fault_hook(cs_server* srv, cs_serve_fault_fn hook, void* user);
 
 #ifdef __cplusplus
 }

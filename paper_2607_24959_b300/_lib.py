@@ -29,8 +29,11 @@ CS_EUNSUPPORTED = -6
 CS_PENDING = 1
 
 ST_OK, ST_MAXITER, ST_CHOLFAIL, ST_NONFINITE, ST_BADSHAPE, ST_NOPROGRESS = range(6)
+ST_FAILED, ST_TIMEOUT = 6, 7
 STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "CHOLFAIL", 3: "NONFINITE",
-                4: "BADSHAPE", 5: "NOPROGRESS", 6: "FAILED"}
+                4: "BADSHAPE", 5: "NOPROGRESS", 6: "FAILED", 7: "TIMEOUT"}
+SERVE_FAULT_H2D, SERVE_FAULT_LAUNCH, SERVE_FAULT_D2H, SERVE_FAULT_COMPLETE = range(4)
+SERVE_FAULT_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p)
 
 
 class CsBatch(ctypes.Structure):
@@ -68,7 +71,7 @@ CS_SERVE_FIXED = 1
 class CsServeConfig(ctypes.Structure):
     _fields_ = [("arena_bytes", c_size_t), ("streams", c_int32), ("max_batch", c_int32),
                 ("policy", c_int32), ("fixed_batch", c_int32), ("tol", c_float),
-                ("max_iter", c_int32), ("max_queue", c_int32), ("reserved", c_int32)]
+                ("max_iter", c_int32), ("max_queue", c_int32), ("queue_timeout_ms", c_int32)]
 
 
 class CsRequest(ctypes.Structure):
@@ -85,7 +88,8 @@ class CsResult(ctypes.Structure):
 class CsServeStats(ctypes.Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("batches", c_int64),
                 ("batched_requests", c_int64), ("queued", c_int64),
-                ("max_inflight", c_int32), ("failed_launches", c_int32)]
+                ("max_inflight", c_int32), ("failed_launches", c_int32),
+                ("timed_out", c_int64)]
 
 # name -> (restype, argtypes)
 _SIGS = {
@@ -165,6 +169,7 @@ _SIGS = {
     "cs_serve_flush": (ctypes.c_int, [c_void_p]),
     "cs_serve_get_stats": (ctypes.c_int, [c_void_p, ctypes.POINTER(CsServeStats)]),
     "cs_serve_destroy": (None, [c_void_p]),
+    "cs_serve_set_fault_hook": (ctypes.c_int, [c_void_p, SERVE_FAULT_FN, c_void_p]),
 }
 
 STATIC_MAX_INSTANCES = 1 << 20

@@ -22,7 +22,8 @@ def _f32(x):
 
 class Server:
     def __init__(self, arena_bytes=1 << 30, streams=4, max_batch=4096, policy="continuous",
-                 fixed_batch=1024, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER, max_queue=0):
+                 fixed_batch=1024, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER, max_queue=0,
+                 queue_timeout_ms=0):
         self._lib = _lib.load()
         c = _lib.CsServeConfig()
         c.arena_bytes = int(arena_bytes)
@@ -33,6 +34,7 @@ class Server:
         c.tol = float(tol)
         c.max_iter = int(max_iter)
         c.max_queue = int(max_queue)
+        c.queue_timeout_ms = int(queue_timeout_ms)
         h = ctypes.c_void_p(None)
         _lib.check(self._lib.cs_serve_create(ctypes.byref(c), ctypes.byref(h)), "cs_serve_create")
         self._h = h
@@ -127,6 +129,19 @@ class Server:
 
     def flush(self):
         _lib.check(self._lib.cs_serve_flush(self._h), "cs_serve_flush")
+
+    def set_fault_hook(self, fn):
+        """Host-side fault injection (cs_serve_set_fault_hook): fn(stage,
+        batch) -> bool, True making that step of that batch fail; None
+        removes it."""
+        if fn is None:
+            self._hook = None
+            cb = _lib.SERVE_FAULT_FN()
+        else:
+            cb = _lib.SERVE_FAULT_FN(lambda stage, batch, user: 1 if fn(stage, batch) else 0)
+            self._hook = cb   # the callback must outlive its use by the scheduler
+        _lib.check(self._lib.cs_serve_set_fault_hook(self._h, cb, None),
+                   "cs_serve_set_fault_hook")
 
     def stats(self) -> dict:
         s = _lib.CsServeStats()

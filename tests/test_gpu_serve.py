@@ -133,3 +133,23 @@ def test_bulk_submit_and_poll_out_of_order(cuda_device):
             assert time.time() - t0 < 60
             time.sleep(1e-3)
     assert all(results[i].status == 0 for i in range(len(reqs)))
+
+
+def test_host_injected_launch_failure_on_the_gpu_server(cuda_device):
+    """The fault hook on the CUDA server: batch 1's kernel launch is made to
+    fail on the host (nothing is issued to the GPU for it); exactly its
+    requests complete with CS_ST_FAILED, and the batches before and after it
+    are solved as usual."""
+    from paper_2607_24959_b300 import _lib
+    reqs = _requests(n=12, seed=71)
+    with serve.Server(arena_bytes=256 << 20, streams=2, policy="fixed",
+                      fixed_batch=4) as srv:
+        srv.set_fault_hook(lambda stage, batch: stage == _lib.SERVE_FAULT_LAUNCH and batch == 1)
+        res = []
+        for w in range(3):
+            res += _wait(srv, [_submit(srv, p) for p in reqs[4 * w:4 * w + 4]])
+        st = srv.stats()
+        srv.set_fault_hook(None)
+    assert [r["status"] for r in res] == [0] * 4 + [_lib.ST_FAILED] * 4 + [0] * 4
+    assert all(not np.any(r["a"]) for r in res[4:8])
+    assert st["failed_launches"] == 1 and st["batches"] == 3
