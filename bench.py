@@ -279,12 +279,13 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
     for tk in wt:
         while srv.poll(tk) is None:
             time.sleep(1e-4)
+    drain = (ctypes.c_uint64 * 8192)()
+    while srv.completed(drain):      # the warm-up's completions are not the stream's
+        pass
     old_switch = sys.getswitchinterval()
     sys.setswitchinterval(1e-4)   # the producer thread must not wait 5 ms for the GIL
     carr = serve.Server.make_requests(reqs)
     tickets = (ctypes.c_uint64 * n)()
-    results = (_lib.CsResult * n)()
-    done = (ctypes.c_int32 * n)()
     submitted = [0]
     t0 = time.monotonic() + 0.05
 
@@ -306,27 +307,38 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
 
     th = threading.Thread(target=producer, daemon=True)
     th.start()
-    lo = 0
+    # collect exactly the tickets the server reports as completed (no scan
+    # of the outstanding ones under the server's lock)
+    t_done = np.zeros(n)
+    status = np.full(n, -1, np.int64)
+    comp = (ctypes.c_uint64 * 8192)()
+    rtmp = (_lib.CsResult * 8192)()
+    dtmp = (ctypes.c_int32 * 8192)()
+    collected = 0
     deadline = time.monotonic() + 120.0 + float(t_arr[-1])
-    while lo < n:
-        hi = min(submitted[0], lo + 8192)
-        if hi > lo:
-            srv.poll_batch(tickets, lo, hi, results, done)
-            while lo < hi and done[lo] == 1:
-                lo += 1
-            if lo < hi and done[lo] < 0:
-                srv.close()
-                raise RuntimeError("serving lost a ticket")
+    while collected < n:
+        k = srv.completed(comp)
+        if k:
+            for i in range(k):
+                dtmp[i] = 0
+            srv.poll_batch(comp, 0, k, rtmp, dtmp)
+            for i in range(k):
+                if dtmp[i] != 1:
+                    srv.close()
+                    raise RuntimeError("serving lost a ticket")
+                idx = int(comp[i]) - int(tickets[0])   # tickets are consecutive
+                t_done[idx] = rtmp[i].t_done
+                status[idx] = rtmp[i].status
+            collected += k
+        else:
+            time.sleep(1e-4)
         if time.monotonic() > deadline:
             srv.close()
-            raise RuntimeError(f"serving did not finish: {lo} of {n} collected")
-        time.sleep(1e-4)
+            raise RuntimeError(f"serving did not finish: {collected} of {n} collected")
     th.join(timeout=10.0)
     sys.setswitchinterval(old_switch)
     st = srv.stats()
     srv.close()
-    t_done = np.array([results[i].t_done for i in range(n)])
-    status = np.array([results[i].status for i in range(n)])
     lat = t_done - (t0 + np.asarray(t_arr))
     span = t_done.max() - (t0 + t_arr[0])
     return {"requests": n, "p50_ms": float(np.percentile(lat, 50) * 1e3),

@@ -488,6 +488,13 @@ int cs_serve_submit_batch(cs_server* srv, int32_t n, const cs_request* reqs,
 int cs_serve_poll_batch(cs_server* srv, int32_t n, const uint64_t* tickets,
                         cs_result* res, int32_t* done);
 
+/* Tickets whose requests completed since the previous call, in completion
+ * order (at most max of them, written to tickets); returns their number.
+ * A client that holds many outstanding tickets collects exactly these with
+ * cs_serve_poll_batch instead of scanning every outstanding one.  Each
+ * completion is reported once. */
+int cs_serve_completed(cs_server* srv, int32_t max, uint64_t* tickets);
+
 /* Drop a request that is still queued (CS_EBUSY once it is on the GPU). */
 int cs_serve_cancel(cs_server* srv, uint64_t ticket);
 

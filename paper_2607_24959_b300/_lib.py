@@ -170,6 +170,7 @@ _SIGS = {
     "cs_serve_get_stats": (ctypes.c_int, [c_void_p, ctypes.POINTER(CsServeStats)]),
     "cs_serve_destroy": (None, [c_void_p]),
     "cs_serve_set_fault_hook": (ctypes.c_int, [c_void_p, SERVE_FAULT_FN, c_void_p]),
+    "cs_serve_completed": (ctypes.c_int, [c_void_p, c_int32, c_void_p]),
 }
 
 STATIC_MAX_INSTANCES = 1 << 20

@@ -4,6 +4,10 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "contact_solve.h"
 
 namespace csk {
@@ -25,6 +29,46 @@ struct KernelInfo {
 };
 
 int set_error(int code, const char* fmt, ...);
+
+// Launch set-up of one kernel, done once per device and shape: the dynamic
+// shared-memory attribute (raised when a larger size is asked for) and the
+// resident blocks per SM of each (block size, shared memory).  A launch
+// pays for these runtime queries only the first time (they cost tens of
+// microseconds, which a serving batch of small instances would pay per
+// bucket launch).
+struct KernelSetup {
+  std::mutex mu;
+  size_t smem_set[16] = {};
+  std::map<std::tuple<int, int, size_t>, int> per_sm;
+};
+
+template <class Kernel>
+cudaError_t kernel_setup(KernelSetup& ks, Kernel kern, int threads, size_t smem, int* per_sm) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(ks.mu);
+  const bool cached = dev >= 0 && dev < 16;
+  if (!cached || ks.smem_set[dev] < smem) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // all of the unified L1/shared array as shared memory: the warps' (or
+    // CTAs') slices are the working set, and occupancy hides the latency
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    if (cached) ks.smem_set[dev] = smem;
+  }
+  const auto key = std::make_tuple(dev, threads, smem);
+  auto it = ks.per_sm.find(key);
+  if (it != ks.per_sm.end()) {
+    *per_sm = it->second;
+    return cudaSuccess;
+  }
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, threads, smem);
+  if (e == cudaSuccess) ks.per_sm[key] = *per_sm;
+  return e;
+}
 int cuda_error(cudaError_t e, const char* where);
 int nv_bucket(int nv);
 int mt_bucket(int m);

@@ -23,14 +23,9 @@ static cudaError_t launch_cta_t(int nv_max, int m_max, const csk::Params& P, cud
   const csk::CtaGeo geo = csk::CtaGeo::make(nv_max, m_max);
   const size_t smem = geo.bytes();
   if (smem > device_smem_optin()) return cudaErrorInvalidConfiguration;
-  cudaError_t e =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
+  static KernelSetup setup;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, csk::kCtaThreads, smem);
+  cudaError_t e = kernel_setup(setup, kern, csk::kCtaThreads, smem, &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)per_sm * device_sm_count();

@@ -17,16 +17,9 @@ static cudaError_t launch_t(const csk::Params& P, const LaunchCfg& cfg, cudaStre
   const size_t optin = device_smem_optin();
   while (wpb > 1 && (size_t)wpb * G::kBytes > optin) --wpb;
   const size_t smem = (size_t)wpb * G::kBytes;
-  cudaError_t e =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  // all of the unified L1/shared array as shared memory: the warps' slices
-  // are the working set, and occupancy is what hides the solver's latency
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
+  static KernelSetup setup;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
+  cudaError_t e = kernel_setup(setup, kern, wpb * 32, smem, &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < per_sm) per_sm = cfg.blocks_per_sm;

@@ -154,6 +154,11 @@ int cs_serve_poll_batch(cs_server* S, int32_t n, const uint64_t* tickets, cs_res
   return S->poll_batch(n, tickets, res, done);
 }
 
+int cs_serve_completed(cs_server* S, int32_t max, uint64_t* tickets) {
+  if (!S) return set_error(CS_EINVAL, "server must not be NULL");
+  return S->take_completed(max, tickets);
+}
+
 int cs_serve_cancel(cs_server* S, uint64_t ticket) {
   if (!S) return set_error(CS_EINVAL, "server must not be NULL");
   return S->cancel(ticket);

@@ -177,6 +177,7 @@ struct Server {
   std::condition_variable cv;
   std::deque<std::shared_ptr<Req>> queue;
   std::unordered_map<uint64_t, std::shared_ptr<Req>> tickets;
+  std::deque<uint64_t> done_list;  // tickets in completion order, not yet reported
   BufPool pool;  // request buffers, returned when a ticket is retired
   uint64_t next_ticket = 1;
   bool stop = false;
@@ -420,6 +421,10 @@ struct Server {
       r.t_done = t;
       r.state.store(2, std::memory_order_release);
     }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (auto& r : sl.reqs) done_list.push_back(r->ticket);
+    }
     completed += n;
     sl.reqs.clear();
     sl.busy = false;
@@ -439,6 +444,7 @@ struct Server {
         r.iters = 0;
         r.t_start = r.t_done = t;
         r.state.store(2, std::memory_order_release);
+        done_list.push_back(r.ticket);
         timed_out++;
         completed++;
         it = queue.erase(it);
@@ -665,6 +671,18 @@ struct Server {
       done[pr.first] = 1;
     }
     return (int)ready.size();
+  }
+
+  // Tickets completed since the last call, in completion order (at most max).
+  int take_completed(int32_t max, uint64_t* out) {
+    if (max < 0 || (max > 0 && !out)) return be.set_error(CS_EINVAL, "tickets must not be NULL");
+    std::lock_guard<std::mutex> lk(mu);
+    int n = 0;
+    while (n < max && !done_list.empty()) {
+      out[n++] = done_list.front();
+      done_list.pop_front();
+    }
+    return n;
   }
 
   int cancel(uint64_t ticket) {

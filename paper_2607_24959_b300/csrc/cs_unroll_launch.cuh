@@ -15,14 +15,9 @@ static cudaError_t launch_unrolled_t(const csk::UParams& U, cudaStream_t s) {
   const size_t optin = device_smem_optin();
   while (wpb > 1 && (size_t)wpb * G::kBytes > optin) --wpb;
   const size_t smem = (size_t)wpb * G::kBytes;
-  cudaError_t e =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
+  static KernelSetup setup;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
+  cudaError_t e = kernel_setup(setup, kern, wpb * 32, smem, &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   long long grid = (long long)per_sm * device_sm_count();

@@ -123,6 +123,13 @@ class Server:
         rc = self._lib.cs_serve_poll_batch(self._h, n, tk, rs, dn)
         return _lib.check(rc, "cs_serve_poll_batch")
 
+    def completed(self, buf, max_n=None) -> int:
+        """Tickets completed since the previous call (cs_serve_completed),
+        written to buf (a ctypes uint64 array); returns their number."""
+        n = len(buf) if max_n is None else int(max_n)
+        rc = self._lib.cs_serve_completed(self._h, n, buf)
+        return _lib.check(rc, "cs_serve_completed")
+
     def cancel(self, ticket: int):
         _lib.check(self._lib.cs_serve_cancel(self._h, ctypes.c_uint64(ticket)), "cs_serve_cancel")
         self._shapes.pop(ticket, None)
