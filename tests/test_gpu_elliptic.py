@@ -51,6 +51,43 @@ def _zone_margin(w, b, a):
     return best
 
 
+def _contact_margins(w, b, a):
+    """Relative zone-boundary distance of every contact at a (as _zone_margin)."""
+    p = {k: np.asarray(v, np.float64) for k, v in w.instance(b).items()}
+    u = p["J"] @ a - p["aref"]
+    sc = np.abs(p["J"]) @ np.abs(a) + np.abs(p["aref"])
+    out = []
+    for c in range(p["J"].shape[0] // 3):
+        uN, t = u[3 * c], np.hypot(u[3 * c + 1], u[3 * c + 2])
+        DN, DT, mu = p["D"][3 * c], p["D"][3 * c + 1], p["mu"][3 * c]
+        s = max(sc[3 * c], sc[3 * c + 1], sc[3 * c + 2])
+        out.append(min(abs(mu * t - uN) / s, abs(mu * DN * uN + DT * t) / (DT * s + mu * DN * s)))
+    return np.array(out)
+
+
+def _traced_to_near_contact(w, b, gpu, ref, s, a):
+    """Whether the instance has a contact within 1e-4 of a zone boundary and
+    that contact's own rows carry entries beyond the tolerance (relative to
+    the output's largest entry) in some per-row output (daref, dJ, dD, dmu):
+    the contact whose zone-dependent terms lose digits is then implicated
+    directly, and other entries' errors are what it passes on through w."""
+    near = np.flatnonzero(_contact_margins(w, b, a) < 1e-4)
+    if near.size == 0:
+        return False
+    nv = int(w.inst[b]["nv"])
+    for k in ("daref", "dD", "dmu", "dJ"):
+        x = np.asarray(gpu[k][s[k]], np.float64)
+        y = np.asarray(ref[k][s[k]], np.float64)
+        if x.size == 0:
+            continue
+        err = np.abs(x - y) / max(np.max(np.abs(y)), 1e-30)
+        rows = err.reshape(-1, nv).max(1) if k == "dJ" else err
+        for c in near:
+            if np.max(rows[3 * c:3 * c + 3]) > parity.G_TOL:
+                return True
+    return False
+
+
 def _check(w, gpu, idx, what, max_flip=0.02):
     ref = oracle.ell_solve_workload(w, idx=idx, threads=8)
     worst = {k: 0.0 for k in ("a",) + KEYS}
@@ -67,11 +104,17 @@ def _check(w, gpu, idx, what, max_flip=0.02):
         errs = {k: parity.rel(gpu[k][s[k]], ref[k][s[k]]) for k in KEYS}
         if any(v > parity.G_TOL for v in errs.values()):
             # the derivative is local to the zones, and near a zone boundary
-            # (relative margin delta) the Hessian blocks change by ~1/delta
-            # per relative change of u: FP32's ~1e-7 error in a then moves
-            # the adjoint by ~1e-7/delta, so instances with delta < 1e-4 are
-            # not held to 1e-3 (they are counted instead)
-            if _zone_margin(w, b, ref["a"][s["a"]]) < 1e-4:
+            # (relative margin delta) the FP32 evaluation of that contact's
+            # zone-dependent adjoint terms loses about log10(1/delta) digits:
+            # an instance whose near-boundary contact itself carries entries
+            # beyond the tolerance is not held to 1e-3 (it is counted
+            # instead); any other error fails
+            # (an instance with such a contact whose errors elsewhere stay
+            # within ten times the tolerance is counted too: the near
+            # contact's error reaches every row through w)
+            if (_traced_to_near_contact(w, b, gpu, ref, s, ref["a"][s["a"]]) or
+                    (_zone_margin(w, b, ref["a"][s["a"]]) < 1e-4 and
+                     max(errs.values()) <= 10 * parity.G_TOL)):
                 flips += 1
                 continue
             bad.append((int(b), errs))
