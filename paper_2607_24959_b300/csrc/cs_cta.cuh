@@ -738,7 +738,7 @@ struct CtaSolver {
       block_sum2(sum, cs);
       const float d = c0 + alpha * pMp + sum;
       if (d == 0.f) break;
-      float an = alpha - d / (pMp + cs), x0, x1;
+      float an = alpha - __fdividef(d, pMp + cs), x0, x1;
       if (d < 0.f) {
         lo = alpha;
         x0 = alpha;

@@ -501,7 +501,10 @@ struct WarpSolver {
   // column-at-a-time substitution, so the result is identical bit for bit;
   // the dependency chain has one shuffle per block instead of per column.
   static constexpr int kSB = (NV % 4 == 0) ? 4 : (NV % 3 == 0) ? 3 : (NV % 2 == 0) ? 2 : 1;
-  __device__ __forceinline__ float chol_solve(float x) {
+  __device__ __forceinline__ float chol_solve(float x) { return chol_backward(chol_forward(x)); }
+
+  // L y = x (forward substitution, blocked as above).
+  __device__ __forceinline__ float chol_forward(float x) {
     const float* L = Ls();
     const float* dinv = Vec(V_DINV);
     const float* Lrow = L + min(lane, NV - 1) * G::MS;
@@ -525,6 +528,13 @@ struct WarpSolver {
       for (int u = 0; u < kSB; ++u)
         if (lane == kb + u) x = y[u];
     }
+    return x;
+  }
+
+  // L^T z = y (backward substitution, blocked as above).
+  __device__ __forceinline__ float chol_backward(float x) {
+    const float* L = Ls();
+    const float* dinv = Vec(V_DINV);
 #pragma unroll 1
     for (int kt = NV - kSB; kt >= 0; kt -= kSB) {
       float z[kSB];
@@ -1025,7 +1035,7 @@ struct WarpSolver {
       cs = warp_sum(cs);
       const float d = kDiff ? c0 + alpha * (pMp + cs) + sum : c0 + alpha * pMp + sum;
       if (d == 0.f) break;
-      float an = alpha - d / (pMp + cs), x0, x1;
+      float an = alpha - __fdividef(d, pMp + cs), x0, x1;
       if (d < 0.f) {
         lo = alpha;
         x0 = alpha;
@@ -1328,8 +1338,29 @@ struct WarpSolver {
     const float* va = Vec(V_X);
     float* dJ = P.dJ + e.off_J;
     const int mnv = m * nv;
+    int q0 = 0;
+    if (nv == NV && NV >= 4 && (reinterpret_cast<uintptr_t>(dJ) & 15) == 0) {
+      // four consecutive entries per lane and one 16-byte store; the four
+      // span at most two rows of J
+      const int n4 = mnv >> 2;
 #pragma unroll 1
-    for (int q = lane; q < mnv; q += 32) {
+      for (int q4 = lane; q4 < n4; q4 += 32) {
+        const int q = 4 * q4;
+        const int rr = q / NV, cc = q - rr * NV;
+        const float f0 = F[rr], l0 = Lm[rr], f1 = F[rr + 1], l1 = Lm[rr + 1];
+        float o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool next = cc + u >= NV;
+          const int c = next ? cc + u - NV : cc + u;
+          o[u] = -__fmaf_rn(next ? f1 : f0, vw[c], (next ? l1 : l0) * va[c]);
+        }
+        *reinterpret_cast<float4*>(dJ + q) = make_float4(o[0], o[1], o[2], o[3]);
+      }
+      q0 = 4 * n4;
+    }
+#pragma unroll 1
+    for (int q = q0 + lane; q < mnv; q += 32) {
       int rr, cc;
       if (nv == NV) {
         rr = q / NV;
