@@ -14,8 +14,8 @@
 //  * Cholesky: blocked right-looking in shared memory over 32-column panels
 //    (warp 0 factors the diagonal block, all threads solve the panel below
 //    it and update the trailing matrix; see factor());
-//  * triangular solves: blocked the same way (warp 0 on each 32 x 32
-//    diagonal block, all threads on the rectangular block beside it).
+//  * triangular solves: one warp, four unknowns per shuffle round, no block
+//    barrier inside (see tri_solve_warp()).
 #pragma once
 
 #include "cs_warp.cuh"
@@ -335,107 +335,102 @@ struct CtaSolver {
     return all_ok;
   }
 
-  // x (shared vector slot `slot`, nvcap entries) <- (L L^T)^-1 x, blocked by
-  // 32 rows: warp 0 solves each diagonal block with shuffles (lane = row);
-  // the coupling to the other blocks is a matrix-vector product spread over
-  // all threads.
-  __device__ __forceinline__ void chol_solve(int slot) {
-    const float* L = Ls();
-    const float* dv = V(C_DINV);
-    float* X = V(slot);
-    const int nc = geo.nvcap, MS = geo.MS;
+  // x <- (L L^T)^-1 x by one warp, with no block barrier inside: lane l
+  // holds x at rows l, l + 32, l + 64, l + 96.  Forward substitution takes
+  // the unknowns four at a time: the four are gathered by shuffles, each lane
+  // solves their 4 x 4 diagonal block itself (the same operations in the same
+  // order as column-at-a-time substitution), and every lane subtracts their
+  // contributions from its own rows below them, one column after the other.
+  // The backward substitution with L^T does the same from the last four
+  // unknowns up, reading L's rows (the transposed entries of each column).
+  // The register index of a lane's rows is fixed in each unrolled copy of
+  // the outer loop, so x stays in registers.
+  //
+  // Measured on the nv96 workload: the blocked version (warp 0 on the
+  // diagonal blocks, all warps on the coupling products, a block barrier
+  // between) took 17 k cycles per solve; one warp alone takes a few thousand.
+  __device__ static __noinline__ void tri_solve_warp(const float* L, const float* dv, float* X,
+                                                     int MS, int nc, int lane) {
+    float xr[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = lane + 32 * j;
+      xr[j] = (r < nc) ? X[r] : 0.f;
+    }
     // forward: L y = x
+#pragma unroll
+    for (int jb = 0; jb < 4; ++jb) {
+      if (32 * jb >= nc) break;
+      const int cend = min(32, nc - 32 * jb);
 #pragma unroll 1
-    for (int kb = 0; kb < nc; kb += 32) {
-      const int bs = min(32, nc - kb);
-      if (warp == 0) {
-        // four unknowns per shuffle round, each lane solving the 4 x 4
-        // diagonal block itself (same operations in the same order as
-        // column-at-a-time substitution)
-        float x = (lane < bs) ? X[kb + lane] : 0.f;
-        const float* Lr = L + (kb + min(lane, bs - 1)) * MS + kb;
-#pragma unroll 1
-        for (int cb = 0; cb < bs; cb += 4) {
-          float y[4];
+      for (int c0 = 0; c0 < cend; c0 += 4) {
+        const int cb = 32 * jb + c0;
+        float y[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) y[u] = __shfl_sync(kFull, x, cb + u);
+        for (int u = 0; u < 4; ++u) y[u] = __shfl_sync(kFull, xr[jb], c0 + u);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float* Lu = L + (kb + cb + u) * MS + kb + cb;
+        for (int u = 0; u < 4; ++u) {
+          const float* Lu = L + (cb + u) * MS + cb;
 #pragma unroll
-            for (int w = 0; w < u; ++w) y[u] = __fmaf_rn(-Lu[w], y[w], y[u]);
-            y[u] = y[u] * dv[kb + cb + u];
-          }
-          if (lane >= cb + 4 && lane < bs) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x = __fmaf_rn(-Lr[cb + u], y[u], x);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (lane == cb + u) x = y[u];
+          for (int w = 0; w < u; ++w) y[u] = __fmaf_rn(-Lu[w], y[w], y[u]);
+          y[u] = y[u] * dv[cb + u];
         }
-        if (lane < bs) X[kb + lane] = x;
-      }
-      __syncthreads();
-      for (int i = kb + bs + tid; i < nc; i += kCtaThreads) {
-        const float* Li = L + i * MS + kb;
-        float t = 0.f, t2 = 0.f;
-        int k = 0;
-        for (; k + 1 < bs; k += 2) {
-          t = __fmaf_rn(Li[k], X[kb + k], t);
-          t2 = __fmaf_rn(Li[k + 1], X[kb + k + 1], t2);
+#pragma unroll
+        for (int j = jb; j < 4; ++j) {
+          const int r = lane + 32 * j;
+          if (r > cb + 3 && r < nc) {
+            const float* Lr = L + r * MS + cb;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xr[j] = __fmaf_rn(-Lr[u], y[u], xr[j]);
+          }
         }
-        if (k < bs) t = __fmaf_rn(Li[k], X[kb + k], t);
-        X[i] -= t + t2;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (lane == c0 + u) xr[jb] = y[u];
       }
-      __syncthreads();
     }
     // backward: L^T x = y
-    const int last = ((nc - 1) / 32) * 32;
+#pragma unroll
+    for (int jb = 3; jb >= 0; --jb) {
+      if (32 * jb >= nc) continue;
+      const int cend = min(32, nc - 32 * jb);
 #pragma unroll 1
-    for (int kb = last; kb >= 0; kb -= 32) {
-      const int bs = min(32, nc - kb);
-      const int below = kb + bs;
-      if (below < nc) {
-        // X[kb + l] -= sum_{j >= below} L[j][kb + l] X[j], 8 threads per row
-        const int l = tid >> 3, q = tid & 7;
-        const int i = kb + min(l, bs - 1);
-        float t = 0.f;
-        for (int j = below + q; j < nc; j += 8) t = __fmaf_rn(L[j * MS + i], X[j], t);
-        t += __shfl_xor_sync(kFull, t, 1);
-        t += __shfl_xor_sync(kFull, t, 2);
-        t += __shfl_xor_sync(kFull, t, 4);
-        __syncthreads();
-        if (q == 0 && l < bs) X[kb + l] -= t;
-        __syncthreads();
-      }
-      if (warp == 0) {
-        float x = (lane < bs) ? X[kb + lane] : 0.f;
-#pragma unroll 1
-        for (int ct = bs - 4; ct >= 0; ct -= 4) {
-          float z[4];
+      for (int c0 = cend - 4; c0 >= 0; c0 -= 4) {
+        const int ct = 32 * jb + c0;
+        float z[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) z[u] = __shfl_sync(kFull, x, ct + u);
+        for (int u = 0; u < 4; ++u) z[u] = __shfl_sync(kFull, xr[jb], c0 + u);
 #pragma unroll
-          for (int u = 3; u >= 0; --u) {
+        for (int u = 3; u >= 0; --u) {
 #pragma unroll
-            for (int w = 3; w > u; --w)
-              z[u] = __fmaf_rn(-L[(kb + ct + w) * MS + kb + ct + u], z[w], z[u]);
-            z[u] = z[u] * dv[kb + ct + u];
-          }
-          if (lane < ct) {
-#pragma unroll
-            for (int w = 3; w >= 0; --w)
-              x = __fmaf_rn(-L[(kb + ct + w) * MS + kb + lane], z[w], x);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (lane == ct + u) x = z[u];
+          for (int w = 3; w > u; --w) z[u] = __fmaf_rn(-L[(ct + w) * MS + ct + u], z[w], z[u]);
+          z[u] = z[u] * dv[ct + u];
         }
-        if (lane < bs) X[kb + lane] = x;
+#pragma unroll
+        for (int j = 0; j <= jb; ++j) {
+          const int r = lane + 32 * j;
+          if (r < ct) {
+#pragma unroll
+            for (int w = 3; w >= 0; --w) xr[j] = __fmaf_rn(-L[(ct + w) * MS + r], z[w], xr[j]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (lane == c0 + u) xr[jb] = z[u];
       }
-      __syncthreads();
     }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = lane + 32 * j;
+      if (r < nc) X[r] = xr[j];
+    }
+  }
+
+  // x (shared vector slot `slot`, nvcap entries) <- (L L^T)^-1 x.  The other
+  // warps wait at the barrier.
+  __device__ __forceinline__ void chol_solve(int slot) {
+    if (warp == 0) tri_solve_warp(Ls(), V(C_DINV), V(slot), geo.MS, geo.nvcap, lane);
+    __syncthreads();
   }
 
   __device__ __forceinline__ bool factor_M() {
@@ -450,7 +445,9 @@ struct CtaSolver {
     return factor();
   }
 
-  // H = M + sum_{active} D_i J_i^T J_i (Eq. 9) into Ls(), then factor.
+  // H = M + sum_{active} D_i J_i^T J_i (Eq. 9) into Ls(), then factor.  4x4
+  // register blocks of the lower triangle, split over groups of active rows
+  // when there are few blocks.
   __device__ __forceinline__ bool assemble_and_factor() {
     const float* Mm = Ms();
     const float* Jm = Js();
@@ -571,12 +568,13 @@ struct CtaSolver {
       s[u] = 0.f;
       c[u] = 0.f;
     }
+    if (32 * warp >= m) return;  // no row of this warp is valid
 #pragma unroll 1
     for (int k = 0; k < nv; ++k) {
       const float xh = vh[k], xl = vl[k];
 #pragma unroll
       for (int u = 0; u < MTC; ++u) {
-        if (kCtaThreads * u < m) {
+        if (kCtaThreads * u + 32 * warp < m) {
           const float a = Jm[min(row(u), m - 1) * JS + k];
           if (precise) dot2(s[u], c[u], a, xh, xl);
           else s[u] = __fmaf_rn(a, xh, s[u]);
@@ -699,12 +697,15 @@ struct CtaSolver {
     const int JS = geo.JS, MS = geo.MS;
 #pragma unroll
     for (int u = 0; u < MTC; ++u) s_r[u] = 0.f;
+    if (32 * warp < m) {  // warps without a valid row skip J p
 #pragma unroll 1
-    for (int k = 0; k < nv; ++k) {
-      const float pk = vp[k];
+      for (int k = 0; k < nv; ++k) {
+        const float pk = vp[k];
 #pragma unroll
-      for (int u = 0; u < MTC; ++u)
-        if (kCtaThreads * u < m) s_r[u] = __fmaf_rn(Jm[min(row(u), m - 1) * JS + k], pk, s_r[u]);
+        for (int u = 0; u < MTC; ++u)
+          if (kCtaThreads * u + 32 * warp < m)
+            s_r[u] = __fmaf_rn(Jm[min(row(u), m - 1) * JS + k], pk, s_r[u]);
+      }
     }
     float pMp = 0.f, c0 = 0.f;
     if (tid < nv) {
