@@ -151,18 +151,23 @@ def algorithmic_work(inst, iters, act_counts):
 # stale and the bench line then reports traffic as null.
 QUADRUPED_STEP_TRAFFIC = {
     "instances": 32768, "read": 242273984, "write": 168365248,
-    "sources_sha1": "9f037bfd6ef613b0ca67f00db1b7008660c24886",
+    "sources_sha1": "08c335e533763a2255dec6461f5ad156f4fc43d1",
     "how": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none "
            "on the full quadruped batch, mean of replays 2-5 of the four bucket kernels"}
 
 
 def kernel_sources_sha1():
-    """Hash of the CUDA sources the warp kernels are built from."""
-    import glob
+    """Hash of the sources the quadruped step's kernels and launches are built
+    from: the warp solver, its launcher and nv = 18 instantiation, the plan,
+    and the public header (the CTA solver, serving and other paths do not
+    run in that step)."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2607_24959_b300", "csrc")
-    for f in sorted(glob.glob(os.path.join(csrc, "*.cu*")) + glob.glob(os.path.join(csrc, "*.h"))):
+    files = [os.path.join(csrc, f) for f in ("cs_warp.cuh", "cs_launch.cuh", "cs_kern_nv18.cu",
+                                             "cs_host.h", "cs_plan.cu")]
+    files.append(os.path.join(ROOT, "include", "contact_solve.h"))
+    for f in files:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
