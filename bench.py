@@ -655,10 +655,12 @@ def run_memory(args):
     this library's kernels: device bytes for differentiating the solve with
     the IFT adjoint (state independent of K) against unrolled reverse mode
     (trace grows with K), through the autograd wrappers, B = 1024 instances.
-    Three sweeps as in the figure's panels, where the sizes fit the
-    one-warp-per-instance kernels of the unrolled path (nv <= 32, m <= 256):
-    step cap K = 1..10 at nv 24 with 4 contacts; contacts 1..64 at nv 6,
-    K = 5; N particles (nv 6N, N contacts) for N = 1..5, K = 5."""
+    The three sweeps of the figure's panels: step cap K = 1..10 at nv 24 with
+    4 contacts; contacts 1..256 at nv 6, K = 5; N particles (nv 6N, N
+    contacts) for N = 1..16, K = 5.  Instances up to nv 32 and 256 rows run
+    one warp each, larger ones one CTA each (both paths).  The paper's two
+    headline ratios (256 contacts at nv 6; 16 particles, nv 96) are printed
+    beside ours."""
     import torch
     from paper_2607_24959_b300 import autograd as csag, solver, workloads as W
 
@@ -730,7 +732,7 @@ def run_memory(args):
     it = out["iterations"]
     it["ift_peak_change_K1_to_K10"] = it["ift_peak"][-1] / it["ift_peak"][0] - 1.0
     it["unrolled_peak_growth_K1_to_K10"] = it["unrolled_peak"][-1] / it["unrolled_peak"][0]
-    ncs = [1, 2, 4, 8, 16, 32, 64]
+    ncs = [1, 2, 4, 8, 16, 32, 64, 128, 256]
     rows = [measure(W.generate(f"mem-c{nc}", 1024, 6, nc, seed=72 + nc, cond=1e2), 5)
             for nc in ncs]
     out["contacts"] = {
@@ -739,7 +741,7 @@ def run_memory(args):
         "unrolled_peak": [r["unrolled"]["peak_bytes"] for r in rows],
         "unrolled_over_ift": [r["unrolled"]["peak_bytes"] / r["ift"]["peak_bytes"]
                               for r in rows]}
-    Ns = [1, 2, 3, 4, 5]
+    Ns = [1, 2, 3, 4, 6, 8, 12, 16]
     rows = [measure(W.generate(f"mem-n{N}", 1024, 6 * N, N, seed=80 + N, cond=1e2), 5)
             for N in Ns]
     out["dof"] = {
@@ -748,6 +750,15 @@ def run_memory(args):
         "unrolled_peak": [r["unrolled"]["peak_bytes"] for r in rows],
         "unrolled_over_ift": [r["unrolled"]["peak_bytes"] / r["ift"]["peak_bytes"]
                               for r in rows]}
+    c, d = out["contacts"], out["dof"]
+    out["headline"] = {
+        "contacts_256_nv6": {"ift_peak": c["ift_peak"][-1], "unrolled_peak": c["unrolled_peak"][-1],
+                             "unrolled_over_ift": c["unrolled_over_ift"][-1], "paper": 20.0},
+        "particles_16_nv96": {"ift_peak": d["ift_peak"][-1], "unrolled_peak": d["unrolled_peak"][-1],
+                              "unrolled_over_ift": d["unrolled_over_ift"][-1], "paper": 6.0},
+        "paper_setting": "compiled temporary memory of JAX/XLA MJX programs, FP64, B 1024, K 5, "
+                         "on a 4 GiB GPU (paper, Fig. 3); here FP32 device bytes of this "
+                         "library's kernels on one B300"}
     # the scaling extremes run one CTA per instance, beyond the unrolled
     # path's one-warp sizes: the IFT adjoint's memory against the step cap
     ext = {"config": "IFT adjoint through the autograd wrapper, step cap K; nv96: nv 96, "

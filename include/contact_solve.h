@@ -391,8 +391,11 @@ int cs_solve_fused_elliptic(const cs_batch* batch, const cs_options* opt,
  * (cs_unrolled_mask_bytes(batch, K) bytes: K x total_r), so it grows
  * linearly with K, unlike cs_state.
  *
- * Sizes: one warp per instance only (nv_max <= 32 and m_max <= 256),
- * CS_EUNSUPPORTED otherwise.  All pointers are device memory; `a`,
+ * Sizes: nv_max <= 128 and m_max <= 1024, one warp per instance up to
+ * nv_max = 32 and m_max = 256 and one 256-thread CTA per instance beyond
+ * (CS_EUNSUPPORTED when one CTA's shared memory cannot hold an instance and
+ * its slots: M, the factor, J and 26 nv-vectors).  All pointers are device
+ * memory; `a`,
  * `status` and `iters` are written by the forward and read by the
  * backward (same batch, same options).  cs_unrolled_bwd uses dJ and dM as
  * accumulators; every output must be non-NULL (daref, dJ, dD may be NULL

@@ -32,7 +32,7 @@ struct CtaGeo {
   int nvcap, mcap;      // capacities (nvcap multiple of 4)
   int MS, JS;           // odd row strides
   int oM, oL, oJ, oD, oF, oLam, oFlo, oLamlo, oIdx, oVec, oScr, oRed, words;
-  __host__ __device__ static CtaGeo make(int nv_max, int m_max) {
+  __host__ __device__ static CtaGeo make(int nv_max, int m_max, int nvec = 13) {
     CtaGeo g;
     g.nvcap = (nv_max + 3) & ~3;
     g.mcap = (m_max + 31) & ~31;
@@ -49,7 +49,7 @@ struct CtaGeo {
     g.oLamlo = g.oFlo + g.mcap;
     g.oIdx = g.oLamlo + g.mcap;
     g.oVec = g.oIdx + g.mcap;
-    g.oScr = g.oVec + 13 * g.nvcap;
+    g.oScr = g.oVec + nvec * g.nvcap;
     // split-K partials: 2 floats per thread for the transposed products, and
     // 16 per (block, row group) for the Newton matrix when it is split
     const int nb = g.nvcap >> 2, nbl = nb * (nb + 1) / 2;
@@ -77,6 +77,7 @@ struct CtaSolver {
   bool fmask_valid;
   float fmax, qmax;
   int rb = 0;  // reduction buffer the next block reduction uses
+  int rlo_slot = -1;  // if set, residual() also writes r's low part there
 
   __device__ __forceinline__ float* Ms() { return sm + geo.oM; }
   __device__ __forceinline__ float* Ls() { return sm + geo.oL; }
@@ -668,10 +669,12 @@ struct CtaSolver {
       const float lo1 = __fadd_rn(e1, mc);
       const float maq = __fadd_rn(t1, lo1);
       two_sum(t1, js, t2, e2);
-      const float r = __fadd_rn(t2, __fadd_rn(lo1, __fadd_rn(e2, jc)));
+      const float tl = __fadd_rn(lo1, __fadd_rn(e2, jc));
+      const float r = __fadd_rn(t2, tl);
       // thread tid reads and overwrites only entry tid of these slots
       V(C_R)[tid] = r;
       V(C_MAQ)[tid] = maq;
+      if (rlo_slot >= 0) V(rlo_slot)[tid] = __fsub_rn(tl, __fsub_rn(r, t2));
       rloc = fabsf(r);
       msm = fabsf(ms);
       jsm = fabsf(js);
@@ -680,6 +683,7 @@ struct CtaSolver {
     for (int j = nv + tid; j < geo.nvcap; j += kCtaThreads) {
       V(C_R)[j] = 0.f;
       V(C_MAQ)[j] = 0.f;
+      if (rlo_slot >= 0) V(rlo_slot)[j] = 0.f;
     }
     const float rm = block_max(rloc);
     const float sc = fmaxf(fmaxf(1.f, qmax), fmaxf(block_max(msm), block_max(jsm)));
@@ -891,17 +895,23 @@ struct CtaSolver {
   }
 
   // ------------------------------------------------------------- adjoint
-  // w = H^-1 g refined with compensated residuals; leaves w in C_WH/C_WL and
-  // lambda in Lam().
-  __device__ __forceinline__ void adjoint() {
-    float* wh = V(C_WH);
-    float* wl = V(C_WL);
+  // w = H^-1 (rhs + rhs_lo) for the factored H and the active list: a first
+  // solve, then refinement with compensated residuals rhs - M w - J^T lambda
+  // (lambda = D_act . (J w), compensated); stops when the untaken correction
+  // moves w by <= step_tol |w| and the active lambda by <= force_tol |lambda|.
+  // Slots: rh / rl the right-hand side's parts (rl < 0: none), oh / ol the
+  // result pair; jh / jl and mh / mr scratch (J^T lambda and M w pairs, mr
+  // also the correction).  Leaves lambda (pair) in Lam() / Lamlo().
+  __device__ __forceinline__ void solve_refined(int rh, int rl, int oh, int ol, int jh, int jl,
+                                                int mh, int mr, float step_tol, float force_tol) {
+    float* wh = V(oh);
+    float* wl = V(ol);
     for (int j = tid; j < geo.nvcap; j += kCtaThreads) {
-      wh[j] = V(C_G)[j];
+      wh[j] = V(rh)[j];
       wl[j] = 0.f;
     }
     __syncthreads();
-    chol_solve(C_WH);
+    chol_solve(oh);
     float* Lm = Lam();
     const float* Jm = Js();
     const float* Mm = Ms();
@@ -929,8 +939,8 @@ struct CtaSolver {
       }
       lmax = block_max(lmax);
       if (it == kAdjointRefineMax) break;
-      float* js_s = V(C_X);
-      float* js_c = V(C_MP);
+      float* js_s = V(jh);
+      float* js_c = V(jl);
       const float* Lml = Lamlo();
       split_dot(nv, nact, true,
                 [&](int j, int q, float& a, float& h, float& l) {
@@ -940,8 +950,8 @@ struct CtaSolver {
                   l = Lml[i];
                 },
                 js_s, js_c);
-      float* ms_s = V(C_P);
-      float* ms_c = V(C_R);
+      float* ms_s = V(mh);
+      float* ms_c = V(mr);
       split_dot(nv, nv, true,
                 [&](int j, int k, float& a, float& h, float& l) {
                   a = Mm[j * MS + k];
@@ -949,21 +959,21 @@ struct CtaSolver {
                   l = wl[k];
                 },
                 ms_s, ms_c);
-      float* rho = V(C_R);
+      float* rho = V(mr);
       float rv = 0.f;
       if (tid < nv) {
         float t1, e1, t2, e2;
-        two_sum(V(C_G)[tid], -ms_s[tid], t1, e1);
+        two_sum(V(rh)[tid], -ms_s[tid], t1, e1);
         two_sum(t1, -js_s[tid], t2, e2);
-        rv = __fadd_rn(t2, __fsub_rn(__fadd_rn(e1, e2), __fadd_rn(ms_c[tid], js_c[tid])));
+        float lo = __fadd_rn(e1, e2);
+        if (rl >= 0) lo = __fadd_rn(lo, V(rl)[tid]);
+        rv = __fadd_rn(t2, __fsub_rn(lo, __fadd_rn(ms_c[tid], js_c[tid])));
       }
       __syncthreads();
       for (int j = tid; j < geo.nvcap; j += kCtaThreads) rho[j] = (j < nv) ? rv : 0.f;
       __syncthreads();
-      chol_solve(C_R);
-      // the correction's size, in w and in the active lambda = D (J dw): when
-      // both are below the adjoint's resolution (kAdjStepTol, kAdjForceTol,
-      // as in the warp solver) w is kept, and lambda already belongs to it
+      chol_solve(mr);
+      // the correction's size, in w and in the active lambda = D (J dw)
       float dm = 0.f, wm = 0.f;
       if (tid < nv) {
         dm = fabsf(rho[tid]);
@@ -971,14 +981,14 @@ struct CtaSolver {
       }
       const float dmax = block_max(dm);
       const float wmax = block_max(wm);
-      if (dmax <= kAdjStepTol * wmax) {
+      if (dmax <= step_tol * wmax) {
         float sd[MTC], cd[MTC];
         rows_dot(rho, rho, false, sd, cd);
         float dl = 0.f;
 #pragma unroll
         for (int u = 0; u < MTC; ++u)
           if ((act_bits >> u) & 1u) dl = fmaxf(dl, fabsf(D_r[u] * sd[u]));
-        if (block_max(dl) <= kAdjForceTol * lmax) break;
+        if (block_max(dl) <= force_tol * lmax) break;
       }
       if (tid < nv) {
         float hh = wh[tid], ll = wl[tid];
@@ -989,6 +999,41 @@ struct CtaSolver {
       __syncthreads();
     }
     __syncthreads();
+  }
+
+  // The IFT adjoint (Eq. 17): w = H^-1 g in C_WH / C_WL, lambda in Lam(),
+  // refined to the adjoint's resolution (kAdjStepTol, kAdjForceTol, as in
+  // the warp solver).
+  __device__ __forceinline__ void adjoint() {
+    solve_refined(C_G, -1, C_WH, C_WL, C_X, C_MP, C_P, C_R, kAdjStepTol, kAdjForceTol);
+  }
+
+  // Active list and bits from a given row mask (rows in order).
+  __device__ __forceinline__ void set_active(uint32_t bits) {
+    int* idx = Idx();
+    float* Rd = Red() + 5 * kCtaWarps;
+    int base = 0;
+#pragma unroll
+    for (int u = 0; u < MTC; ++u) {
+      if (kCtaThreads * u < m) {
+        const bool on = row_valid(u) && ((bits >> u) & 1u);
+        const unsigned bal = __ballot_sync(kFull, on);
+        if (lane == 0) Rd[warp] = __int_as_float(__popc(bal));
+        __syncthreads();
+        int before = base, total = base;
+#pragma unroll
+        for (int w = 0; w < kCtaWarps; ++w) {
+          const int cw = __float_as_int(Rd[w]);
+          if (w < warp) before += cw;
+          total += cw;
+        }
+        if (on) idx[before + __popc(bal & ((1u << lane) - 1u))] = row(u);
+        base = total;
+        __syncthreads();
+      }
+    }
+    nact = base;
+    act_bits = bits;
   }
 
   __device__ __forceinline__ void write_grads(const Params& P, const cs_inst& e) {

@@ -1,5 +1,6 @@
 // cs_unroll_api.cu -- C entry points of the unrolled-differentiation
-// comparison path (forward with trace, reverse sweep).
+// comparison path (forward with trace, reverse sweep): one warp per instance
+// for nv <= 32 and m <= 256, one CTA per instance beyond.
 #include <cuda_runtime.h>
 
 #include "contact_solve.h"
@@ -14,6 +15,9 @@ extern template cudaError_t launch_unrolled_nv<3>(int, int, const csk::UParams&,
 extern template cudaError_t launch_unrolled_nv<9>(int, int, const csk::UParams&, cudaStream_t);
 extern template cudaError_t launch_unrolled_nv<18>(int, int, const csk::UParams&, cudaStream_t);
 extern template cudaError_t launch_unrolled_nv<32>(int, int, const csk::UParams&, cudaStream_t);
+cudaError_t launch_unrolled_cta(int dir, int nv_max, int m_max, const csk::UParams& U,
+                                cudaStream_t s);
+size_t cta_unrolled_smem_bytes(int nv_max, int m_max);
 
 namespace {
 
@@ -24,15 +28,19 @@ int64_t slot_floats(const cs_batch* b) {
 int check_unrolled(const cs_batch* b, const cs_options* o) {
   int rc = check_batch_shapes(b, o);
   if (rc != CS_OK || b->n == 0) return rc;
-  if (!uses_warp_kernel(b->nv_max, b->m_max))
+  if (!uses_warp_kernel(b->nv_max, b->m_max) &&
+      cta_unrolled_smem_bytes(b->nv_max, b->m_max) > device_smem_optin())
     return set_error(CS_EUNSUPPORTED,
-                     "unrolled differentiation runs one warp per instance: nv_max <= 32 and "
-                     "m_max <= 256 (got %d, %d)",
-                     b->nv_max, b->m_max);
+                     "unrolled differentiation: nv_max = %d with m_max = %d needs %zu bytes of "
+                     "shared memory per CTA (limit %zu)",
+                     b->nv_max, b->m_max, cta_unrolled_smem_bytes(b->nv_max, b->m_max),
+                     device_smem_optin());
   return CS_OK;
 }
 
 cudaError_t launch_unrolled(int dir, const cs_batch* b, const csk::UParams& U, cudaStream_t s) {
+  if (!uses_warp_kernel(b->nv_max, b->m_max))
+    return launch_unrolled_cta(dir, b->nv_max, b->m_max, U, s);
   const int nvb = nv_bucket(b->nv_max), mt = mt_bucket(b->m_max);
   switch (nvb) {
     case 3: return launch_unrolled_nv<3>(dir, mt, U, s);
