@@ -361,9 +361,10 @@ int cs_autotune_cache_load(const char* text);
  * dqfrc = w, daref = hess (J w) per contact, dJ = -(grad s w^T + daref a^T)
  * and, where non-NULL, dM (symmetric M, as cs_solve_fused_theta), dD
  * (dL/dD_N on row 3c, dL/dD_T on row 3c+1, 0 on 3c+2) and dmu (dL/dmu_c on
- * row 3c, 0 on the tangent rows).  Sizes: one warp per instance (nv_max <= 32,
- * m_max <= 256), CS_EUNSUPPORTED otherwise.  Workspace, order and errors as
- * for cs_solve_fused. */
+ * row 3c, 0 on the tangent rows).  Sizes: nv_max <= 128 and m_max <= 1024,
+ * one warp per instance up to nv_max = 32 and m_max = 256 and one 256-thread
+ * CTA per instance beyond (CS_EUNSUPPORTED when one CTA's shared memory cannot
+ * hold an instance).  Workspace, order and errors as for cs_solve_fused. */
 int cs_solve_fused_elliptic(const cs_batch* batch, const cs_options* opt,
                             const float* mu, const float* g,
                             const int32_t* order, float* a, float* dqfrc,

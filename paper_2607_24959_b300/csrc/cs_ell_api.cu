@@ -1,4 +1,6 @@
-// cs_ell_api.cu -- C entry point of the round-cone fused solve and adjoint.
+// cs_ell_api.cu -- C entry point of the round-cone fused solve and adjoint:
+// one warp per instance for nv <= 32 and m <= 256, one CTA per instance
+// beyond.
 #include <cuda_runtime.h>
 
 #include "contact_solve.h"
@@ -17,6 +19,8 @@ extern template cudaError_t launch_ell_nv<18>(int, const csk::EParams&, const La
                                               cudaStream_t);
 extern template cudaError_t launch_ell_nv<32>(int, const csk::EParams&, const LaunchCfg&,
                                               cudaStream_t);
+cudaError_t launch_ell_cta(int nv_max, int m_max, const csk::EParams& EP, cudaStream_t s);
+size_t cta_elliptic_smem_bytes(int nv_max, int m_max);
 
 }  // namespace cs
 
@@ -30,11 +34,13 @@ extern "C" int cs_solve_fused_elliptic(const cs_batch* batch, const cs_options* 
                                        size_t workspace_bytes, void* stream) {
   int rc = check_batch_shapes(batch, opt);
   if (rc != CS_OK || batch->n == 0) return rc;
-  if (!uses_warp_kernel(batch->nv_max, batch->m_max))
+  const bool warp = uses_warp_kernel(batch->nv_max, batch->m_max);
+  if (!warp && cta_elliptic_smem_bytes(batch->nv_max, batch->m_max) > device_smem_optin())
     return set_error(CS_EUNSUPPORTED,
-                     "the round-cone solve runs one warp per instance: nv_max <= 32 and "
-                     "m_max <= 256 (got %d, %d)",
-                     batch->nv_max, batch->m_max);
+                     "round cone: nv_max = %d with m_max = %d needs %zu bytes of shared memory "
+                     "per CTA (limit %zu)",
+                     batch->nv_max, batch->m_max,
+                     cta_elliptic_smem_bytes(batch->nv_max, batch->m_max), device_smem_optin());
   if (!g || !a || !dqfrc || !status || !iters ||
       (batch->m_max > 0 && (!daref || !dJ || !mu)))
     return set_error(CS_EINVAL, "mu, g and the output arrays must not be NULL");
@@ -60,6 +66,10 @@ extern "C" int cs_solve_fused_elliptic(const cs_batch* batch, const cs_options* 
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return cuda_error(e, "cs_solve_fused_elliptic counter reset");
+  if (!warp) {
+    e = launch_ell_cta(batch->nv_max, batch->m_max, EP, s);
+    return e == cudaSuccess ? CS_OK : launch_error(e, "cs_solve_fused_elliptic launch");
+  }
   LaunchCfg cfg;
   cfg.warps_per_block = opt->warps_per_block;
   const int mt = mt_bucket(batch->m_max);
