@@ -777,33 +777,42 @@ def run_memory(args):
 def run_elliptic(args):
     """The same workload shape with MuJoCo's round cone (three rows per
     contact, Eqs. 2-5): one fused launch of cs_solve_fused_elliptic per step
-    over the 32768-instance batch, cost-ordered claims, CUDA-event timed on
-    its stream after warm-up."""
+    over the 32768-instance batch (one warp per instance), cost-ordered
+    claims, CUDA-event timed on its stream after warm-up; and the paper's
+    16-particle size (nv 96, 16 round-cone contacts, one CTA per instance,
+    2048 instances) the same way."""
     import torch
     from paper_2607_24959_b300 import solver, workloads as W
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+
+    def timed(w, max_steps):
+        batch = solver.DeviceBatch.from_workload(w, dev)
+        g = torch.from_numpy(w.g).to(dev)
+        mu = torch.from_numpy(w.mu).to(dev)
+        order = torch.from_numpy(solver.cost_order(w.inst)).to(dev)
+        out = solver.solve_fused_elliptic(batch, g, mu, order=order, tol=args.tol)
+        stream = torch.cuda.Stream(device=dev)
+        steps = max(3, min(args.steps, max_steps))
+        with torch.cuda.stream(stream):
+            for _ in range(max(args.warmup, 3)):
+                solver.solve_fused_elliptic(batch, g, mu, order=order, tol=args.tol, out=out)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                solver.solve_fused_elliptic(batch, g, mu, order=order, tol=args.tol, out=out)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        st = out.fused.status.cpu().numpy()[:w.n]
+        it = out.fused.iters.cpu().numpy()[:w.n]
+        del out, batch
+        torch.cuda.empty_cache()
+        return ms, steps, st, it
+
     w = W.quadruped_elliptic()
-    batch = solver.DeviceBatch.from_workload(w, dev)
-    g = torch.from_numpy(w.g).to(dev)
-    mu = torch.from_numpy(w.mu).to(dev)
-    order = torch.from_numpy(solver.cost_order(w.inst)).to(dev)
-    out = solver.solve_fused_elliptic(batch, g, mu, order=order, tol=args.tol)
-    stream = torch.cuda.Stream(device=dev)
-    steps = max(3, min(args.steps, 50))
-    with torch.cuda.stream(stream):
-        for _ in range(max(args.warmup, 3)):
-            solver.solve_fused_elliptic(batch, g, mu, order=order, tol=args.tol, out=out)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            solver.solve_fused_elliptic(batch, g, mu, order=order, tol=args.tol, out=out)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    st = out.fused.status.cpu().numpy()[:w.n]
-    it = out.fused.iters.cpu().numpy()[:w.n]
+    ms, steps, st, it = timed(w, 50)
     res = {"metric": "round-cone fwd+IFT-adjoint solves/s (all parameter gradients)",
            "value": w.n / (ms / 1e3), "unit": "solves/s", "ms_per_step": ms, "steps": steps,
            "config": {"workload": "quadruped_elliptic", "instances": w.n, "nv": 18,
@@ -811,8 +820,16 @@ def run_elliptic(args):
            "status_counts": np.bincount(st, minlength=6).tolist(),
            "iters_mean": float(it.mean()), "iters_max": int(it.max()),
            "gpu_launches_per_step": 1}
-    del out, batch
-    torch.cuda.empty_cache()
+    w = W.generate("nv96_elliptic", 2048, 96, 16, seed=97, cond=1e3, cone="elliptic")
+    ms, steps, st, it = timed(w, 20)
+    res["nv96"] = {"value": w.n / (ms / 1e3), "unit": "solves/s", "ms_per_step": ms,
+                   "steps": steps,
+                   "config": {"workload": "nv96_elliptic", "instances": w.n, "nv": 96,
+                              "contacts": 16, "rows": 48, "cond_M": 1e3,
+                              "kernel": "one CTA per instance"},
+                   "status_counts": np.bincount(st, minlength=6).tolist(),
+                   "iters_mean": float(it.mean()), "iters_max": int(it.max()),
+                   "gpu_launches_per_step": 1}
     return res
 
 
