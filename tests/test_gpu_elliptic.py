@@ -188,3 +188,25 @@ def test_cta_elliptic_on_warp_sized_instances(cuda_device):
                name="quadruped+big elliptic")
     gpu = _gpu(w, cuda_device)
     _check(w, gpu, np.arange(w.n), "quadruped elliptic on the CTA kernel")
+
+
+def test_elliptic_cta_edge_cases(cuda_device):
+    """CTA-sized round-cone batches with no contacts, frictionless contacts
+    (mu = 0), one contact, and a row count that is not a multiple of 3 (a
+    shape error for that instance only)."""
+    parts = []
+    for gen in (lambda: W.generate("c0", 6, 40, 0, seed=103, cond=1e2, cone="elliptic"),
+                lambda: W.generate("cmu0", 6, 40, 8, seed=104, cond=1e2, cone="elliptic",
+                                   mu_lo=0.0, mu_hi=0.0),
+                lambda: W.generate("c1", 6, 64, 1, seed=105, cond=1e2, cone="elliptic")):
+        ww = gen()
+        parts += [ww.instance(b) for b in range(ww.n)]
+    w = W.pack(parts, name="elliptic-cta-edges")
+    gpu = _gpu(w, cuda_device)
+    # many DoF per contact puts contacts onto zone boundaries (as at nv 96):
+    # the per-instance bound holds, the count beyond 1e-3 is not capped
+    _check(w, gpu, np.arange(w.n), "elliptic CTA edge cases", max_over=1.0)
+    bad = W.pack([dict(M=np.eye(40), J=np.ones((4, 40)), qfrc=np.zeros(40), aref=np.zeros(4),
+                       D=np.ones(4), g=np.ones(40), mu=np.ones(4))])
+    out = _gpu(bad, cuda_device)
+    assert out["status"][0] == 4

@@ -209,3 +209,20 @@ def test_unrolled_autograd_and_memory_growth(cuda_device):
     assert np.all(steps == steps[0]) and steps[0] > 0
     assert len(set(ift)) == 1
     print("state bytes K=1..10: unrolled", unrolled, "IFT", ift[0])
+
+
+def test_unrolled_cta_edge_cases(cuda_device):
+    """CTA-sized instances without rows (a = M^-1 qfrc after one exact step
+    or none) and with one row, mixed in one batch, at K = 1 and K = 3."""
+    parts = []
+    for gen in (lambda: W.generate("u-c0", 6, 48, 0, seed=106, cond=1e2),
+                lambda: W.generate("u-c1", 6, 40, 1, seed=107, cond=1e2),
+                lambda: W.generate("u-c4", 6, 33, 4, seed=108, cond=1e2)):
+        ww = gen()
+        parts += [ww.instance(b) for b in range(ww.n)]
+    w = W.pack(parts, name="unrolled-cta-edges")
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    for K in (1, 3):
+        gpu = _gpu_unrolled(batch, w, K)
+        ref = oracle.unrolled_workload(w, K, threads=8)
+        _compare(w, gpu, ref, f"unrolled CTA edge cases K={K}", K, max_bad_frac=0.0)
