@@ -6,8 +6,9 @@
 // 17): each contact's zone, gradient in float-pair arithmetic and 3 x 3
 // Hessian block from cone_eval(); H = M + sum_c J_c^T hess_c J_c; the convex
 // line search by safeguarded Newton on phi' with the quadratic model near
-// convergence; Newton directions and the adjoint from refined solves; the
-// cone parameters' gradients.  The work is spread over the block: rows as in
+// convergence; Newton directions from one FP32 solve of the compensated
+// residual; the adjoint from a refined solve; the cone parameters'
+// gradients.  The work is spread over the block: rows as in
 // the CTA solver (thread t owns rows t + 256 u), contact c owned by thread
 // c mod 256 (at most two per thread), the Newton matrix in 4 x 4 register
 // blocks split over contact groups, and the CTA solver's factor, triangular
@@ -22,8 +23,6 @@ namespace csk {
 // Vector slots beyond the CTA solver's own (CtaVec).
 enum CtaEllVec {
   CE_RLO = C_PP + 1,  // low part of the residual r
-  CE_PL,              // low part of p
-  CE_RH, CE_RL,       // right-hand side of the Newton solve (-r pair)
   CE_S1, CE_S2,       // J^T lambda pair in the refined solve
   CE_RHO,             // the refined solve's correction
   CE_NVEC
@@ -420,9 +419,9 @@ struct CtaElliptic {
   // oh / ol); lambda_c = hess_c (J w)_c (compensated) in Lam / Lamlo per row.
   // `full` refines to the float-pair precision of w (the adjoint: the cone
   // parameters' derivatives carry the small component of J w along a
-  // contact's stiff direction); otherwise to FP32 precision (a Newton
-  // direction).  The stop test is the warp kernel's: the correction taken
-  // last and the change of lambda.
+  // contact's stiff direction); otherwise to FP32 precision.  The stop test
+  // is the warp kernel's: the correction taken last and the change of
+  // lambda.
   __device__ __forceinline__ void solve_refined(int rh, int rl, int oh, int ol, bool full) {
     const float step_tol = full ? 1e-12f : kStepTol;
     const float force_tol = full ? 1e-10f : kForceTol;
@@ -558,13 +557,12 @@ struct CtaElliptic {
       if (stall >= 3) return CS_ST_OK;
       if (k >= P.max_iter) return CS_ST_MAXITER;
       if (!assemble_and_factor()) return CS_ST_CHOLFAIL;
-      // Newton direction from the refined solve of H p = -(r + rlo)
-      for (int j = tid; j < S.geo.nvcap; j += kCtaThreads) {
-        S.V(CE_RH)[j] = -S.V(C_R)[j];
-        S.V(CE_RL)[j] = -S.V(CE_RLO)[j];
-      }
+      // Newton direction: one FP32 solve of H p = -r with the factor (the
+      // residual is compensated and decides every stop test, as in the warp
+      // kernel)
+      for (int j = tid; j < S.geo.nvcap; j += kCtaThreads) pv[j] = -S.V(C_R)[j];
       __syncthreads();
-      solve_refined(CE_RH, CE_RL, C_P, CE_PL, false);
+      S.chol_solve(C_P);
       const float ptr = S.block_sum(tid < nv ? pv[tid] * S.V(C_R)[tid] : 0.f);
       const float amax = S.block_max(tid < nv ? fabsf(ah[tid]) : 0.f);
       if (!(ptr < 0.f)) {
