@@ -164,3 +164,29 @@ def test_library_owned_state_without_gpu(lib):
     lib.cs_state_free(st)
     # after cs_state_free the pointer is no longer a state of the library
     assert lib.cs_state_status(st, None, None, None) == _lib.CS_EINVAL
+
+
+def test_cta_sized_comparator_and_round_cone_checks_without_gpu(lib):
+    """The unrolled comparator and the round cone take CTA-sized batches
+    (nv <= 128, m <= 1024) and refuse, on the host, the ones whose instance
+    does not fit one CTA's shared memory; argument checks come first."""
+    f = ctypes.c_void_p(0x30000)
+    big = _batch(nv_max=128, m_max=1024)
+    o = _opts()
+    # unrolled forward: NULL outputs are refused before any size question
+    assert lib.cs_unrolled_fwd(ctypes.byref(_batch(nv_max=96, m_max=64)), ctypes.byref(o),
+                               None, None, None, None, None, None) == _lib.CS_EINVAL
+    assert lib.cs_unrolled_fwd(ctypes.byref(big), ctypes.byref(o), f, f, f, f, f,
+                               None) == _lib.CS_EUNSUPPORTED
+    assert b"shared memory" in lib.cs_last_error()
+    assert lib.cs_unrolled_fwd(ctypes.byref(_batch(m_max=1025)), ctypes.byref(o), f, f, f, f, f,
+                               None) == _lib.CS_EUNSUPPORTED
+    # round cone: the same size rule
+    assert lib.cs_solve_fused_elliptic(ctypes.byref(big), ctypes.byref(o), f, f, None, f, f, f,
+                                       f, f, f, f, f, f, ctypes.c_void_p(0x20000), 256,
+                                       None) == _lib.CS_EUNSUPPORTED
+    assert b"shared memory" in lib.cs_last_error()
+    # the trace sizes are host arithmetic on the batch totals
+    b = _batch(nv_max=96, m_max=64)
+    assert lib.cs_unrolled_trace_floats(ctypes.byref(b), 5) == 5 * (1000 + 4 * 1000 + 2 * 4)
+    assert lib.cs_unrolled_mask_bytes(ctypes.byref(b), 5) == 5 * 1000
