@@ -142,6 +142,69 @@ def algorithmic_work(inst, iters, act_counts):
     return float(flops.sum()), float(byts.sum())
 
 
+def elliptic_work(inst, iters, act_contacts):
+    """Algorithmic FLOPs and bytes of one round-cone fused solve per instance
+    (sums over the batch), k its Newton steps and c_act its contacts outside
+    zone 0 at the returned point, m = 3 nc.  FLOPs: a0 = nv^3/3 + 2 nv^2; per
+    step the residual 2 m nv (J a) + 2 nv^2 (M a) + 6 c_act nv (J^T grad) +
+    40 nc (cone evaluation), the Newton matrix c_act (18 nv + 3 nv (nv+1))
+    (hess J_c, then J_c^T of it, lower triangle), nv^3/3 + 2 nv^2 (factor and
+    solves), and the line search 2 m nv + 2 nv^2 + 40 nc (one evaluation
+    counted); the adjoint 2 nv^2 + 4 m nv, the gradients 2 m nv + 2 nv^2 +
+    30 nc.  Bytes (4 B each): read M lower, J, qfrc, g, aref, D, mu; write a,
+    dqfrc, daref, dD, dmu, dJ and dM."""
+    nv = inst["nv"].astype(np.float64)
+    m = inst["m"].astype(np.float64)
+    nc = m / 3
+    k = iters.astype(np.float64)
+    ca = act_contacts.astype(np.float64)
+    per_it = (2 * m * nv + 2 * nv ** 2 + 6 * ca * nv + 40 * nc
+              + ca * (18 * nv + 3 * nv * (nv + 1)) + nv ** 3 / 3 + 2 * nv ** 2
+              + 2 * m * nv + 2 * nv ** 2 + 40 * nc)
+    flops = nv ** 3 / 3 + 2 * nv ** 2 + k * per_it + 2 * nv ** 2 + 4 * m * nv \
+        + 2 * m * nv + 2 * nv ** 2 + 30 * nc
+    byts = 4 * (nv * (nv + 1) / 2 + m * nv + 2 * nv + 3 * m
+                + 2 * nv + 3 * m + m * nv + nv * nv)
+    return float(flops.sum()), float(byts.sum())
+
+
+def ncg_work(inst, iters, act_counts):
+    """Algorithmic FLOPs of the conjugate-gradient forward plus the IFT
+    adjoint per instance (sums over the batch), k its CG steps: a0 and the
+    factor of M nv^3/3 + 2 nv^2; per step the residual 2 m nv + 2 m_act nv +
+    2 nv^2, the M^-1 preconditioner 2 nv^2, the line search 2 m nv + 2 nv^2 +
+    8 m; the adjoint's Newton matrix m_act nv (nv+1), its factor and solve
+    nv^3/3 + 2 nv^2, and 2 nv^2 + 4 m nv.  Bytes as the Newton path's."""
+    nv = inst["nv"].astype(np.float64)
+    m = inst["m"].astype(np.float64)
+    k = iters.astype(np.float64)
+    ma = act_counts.astype(np.float64)
+    per_it = 2 * m * nv + 2 * ma * nv + 2 * nv ** 2 + 2 * nv ** 2 + 2 * m * nv + 2 * nv ** 2 + 8 * m
+    flops = (nv ** 3 / 3 + 2 * nv ** 2 + k * per_it + ma * nv * (nv + 1) + nv ** 3 / 3
+             + 2 * nv ** 2 + 2 * nv ** 2 + 4 * m * nv)
+    byts = 4 * (nv * (nv + 1) / 2 + m * nv + 2 * nv + 2 * m + 2 * nv + m + m * nv)
+    return float(flops.sum()), float(byts.sum())
+
+
+def roofline_obj(flops, byts, t_s, dev):
+    """The roofline object of a leg: the larger of its FP32 and HBM
+    fractions (measured peaks) names the bound."""
+    import torch
+    peaks, _ = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    frac_alu = flops / t_s / 1e12 / fp32_peak
+    frac_hbm = byts / t_s / 1e9 / hbm_peak
+    alu = frac_alu >= frac_hbm
+    return {"bound": "alu" if alu else "hbm",
+            "achieved": flops / t_s / 1e12 if alu else byts / t_s / 1e9,
+            "peak": fp32_peak if alu else hbm_peak,
+            "unit": "TFLOP/s" if alu else "GB/s", "frac": max(frac_alu, frac_hbm),
+            "traffic": None, "hbm_frac": frac_hbm, "alu_frac": frac_alu,
+            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts}
+
+
 # DRAM bytes (read + write) of one step of the fused warp kernels on the
 # 32768-instance quadruped batch: ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of the four bucket kernels of the second of two
@@ -809,21 +872,27 @@ def run_elliptic(args):
         ms = e0.elapsed_time(e1) / steps
         st = out.fused.status.cpu().numpy()[:w.n]
         it = out.fused.iters.cpu().numpy()[:w.n]
+        daref = out.fused.daref.cpu().numpy()
+        # contacts outside zone 0 at the returned point: nonzero lambda rows
+        ca = np.array([np.count_nonzero(np.abs(daref[o:o + mm]).reshape(-1, 3).sum(1))
+                       if mm else 0 for o, mm in zip(w.inst["off_r"], w.inst["m"])])
+        flops, byts = elliptic_work(w.inst, it, ca)
+        roof = roofline_obj(flops, byts, ms / 1e3, dev)
         del out, batch
         torch.cuda.empty_cache()
-        return ms, steps, st, it
+        return ms, steps, st, it, roof
 
     w = W.quadruped_elliptic()
-    ms, steps, st, it = timed(w, 50)
+    ms, steps, st, it, roof = timed(w, 50)
     res = {"metric": "round-cone fwd+IFT-adjoint solves/s (all parameter gradients)",
            "value": w.n / (ms / 1e3), "unit": "solves/s", "ms_per_step": ms, "steps": steps,
            "config": {"workload": "quadruped_elliptic", "instances": w.n, "nv": 18,
                       "contacts": "U{0..32}, 3 rows each", "mu": "U(0.2, 1.2)"},
            "status_counts": np.bincount(st, minlength=6).tolist(),
            "iters_mean": float(it.mean()), "iters_max": int(it.max()),
-           "gpu_launches_per_step": 1}
+           "gpu_launches_per_step": 1, "roofline": roof}
     w = W.generate("nv96_elliptic", 2048, 96, 16, seed=97, cond=1e3, cone="elliptic")
-    ms, steps, st, it = timed(w, 20)
+    ms, steps, st, it, roof = timed(w, 20)
     res["nv96"] = {"value": w.n / (ms / 1e3), "unit": "solves/s", "ms_per_step": ms,
                    "steps": steps,
                    "config": {"workload": "nv96_elliptic", "instances": w.n, "nv": 96,
@@ -831,7 +900,7 @@ def run_elliptic(args):
                               "kernel": "one CTA per instance"},
                    "status_counts": np.bincount(st, minlength=6).tolist(),
                    "iters_mean": float(it.mean()), "iters_max": int(it.max()),
-                   "gpu_launches_per_step": 1}
+                   "gpu_launches_per_step": 1, "roofline": roof}
     return res
 
 
@@ -862,12 +931,17 @@ def run_ncg(args):
     ms = e0.elapsed_time(e1) / steps
     st = out.status.cpu().numpy()[:w.n]
     it = out.iters.cpu().numpy()[:w.n]
+    daref = out.daref.cpu().numpy()
+    act = np.array([np.count_nonzero(daref[o:o + mm]) for o, mm in
+                    zip(w.inst["off_r"], w.inst["m"])])
+    flops, byts = ncg_work(w.inst, it, act)
     res = {"metric": "fwd+IFT-adjoint solves/s with the conjugate-gradient forward solver",
            "value": w.n / (ms / 1e3), "unit": "solves/s", "ms_per_step": ms, "steps": steps,
            "config": {"workload": "quadruped", "instances": w.n,
                       "max_iter": solver.NCG_MAX_ITER},
            "status_counts": np.bincount(st, minlength=6).tolist(),
-           "iters_mean": float(it.mean()), "iters_max": int(it.max())}
+           "iters_mean": float(it.mean()), "iters_max": int(it.max()),
+           "roofline": roofline_obj(flops, byts, ms / 1e3, dev)}
     del out, batch
     torch.cuda.empty_cache()
     return res
