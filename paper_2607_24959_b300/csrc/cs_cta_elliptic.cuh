@@ -423,8 +423,8 @@ struct CtaElliptic {
   // is the warp kernel's: the correction taken last and the change of
   // lambda.
   __device__ __forceinline__ void solve_refined(int rh, int rl, int oh, int ol, bool full) {
-    const float step_tol = full ? 1e-12f : kStepTol;
-    const float force_tol = full ? 1e-10f : kForceTol;
+    const float step_tol = full ? 1e-9f : kStepTol;
+    const float force_tol = full ? 1e-7f : kForceTol;
     const int it_max = full ? 2 * kAdjointRefineMax : kAdjointRefineMax;
     const int tid = S.tid, nv = S.nv;
     float* wh = S.V(oh);

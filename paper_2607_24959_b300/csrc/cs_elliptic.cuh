@@ -483,14 +483,16 @@ struct EllipticSolver {
 
   // ------------------------------------------------------------ adjoint
   // H w = rhs + rhs_lo with refinement; lambda_c = hess_c (J w)_c
-  // (compensated) in Lam / Lamlo per row.  `full` refines to the float-pair
-  // precision of w (the adjoint: the cone parameters' derivatives carry the
-  // small component of J w along a contact's stiff direction, about 1e-4 of
-  // the rest); otherwise to FP32 precision.
+  // (compensated) in Lam / Lamlo per row.  `full` refines beyond FP32 (the
+  // adjoint: the cone parameters' derivatives carry the small component of
+  // J w along a contact's stiff direction, about 1e-4 of the rest), to a
+  // correction of 1e-9 |w| and a change of lambda of 1e-7 |lambda| (1e-12 /
+  // 1e-10 cost 5 % of the solve for the same gradients); otherwise to FP32
+  // precision.
   __device__ __forceinline__ void solve_refined(float rhs, float rhs_lo, float& wh, float& wl,
                                                 bool full = false) {
-    const float step_tol = full ? 1e-12f : kStepTol;
-    const float force_tol = full ? 1e-10f : kForceTol;
+    const float step_tol = full ? 1e-9f : kStepTol;
+    const float force_tol = full ? 1e-7f : kForceTol;
     const int it_max = full ? 2 * kAdjointRefineMax : kAdjointRefineMax;
     const int lane = S.lane;
     wh = S.chol_solve(rhs);
