@@ -882,7 +882,7 @@ def run_elliptic(args):
         torch.cuda.empty_cache()
         return ms, steps, st, it, roof
 
-    w = W.quadruped_elliptic()
+    w = W.quadruped_elliptic(n=args.elliptic_n)
     ms, steps, st, it, roof = timed(w, 50)
     res = {"metric": "round-cone fwd+IFT-adjoint solves/s (all parameter gradients)",
            "value": w.n / (ms / 1e3), "unit": "solves/s", "ms_per_step": ms, "steps": steps,
@@ -998,6 +998,8 @@ def main():
                     help="skip the conjugate-gradient forward solver leg")
     ap.add_argument("--no-elliptic", action="store_true",
                     help="skip the round-cone throughput leg")
+    ap.add_argument("--elliptic-n", type=int, default=32768,
+                    help="instances of the round-cone leg's quadruped batch")
     ap.add_argument("--no-memory", action="store_true",
                     help="skip the IFT vs unrolled differentiation memory sweeps")
     ap.add_argument("--warmup-seconds", type=float, default=0.5,
