@@ -539,7 +539,7 @@ struct CtaSolver {
     const int col = tid % max(ncols, 1), grp = tid / max(ncols, 1);
     float s = 0.f, c = 0.f;
     if (grp < R && col < ncols) {
-#pragma unroll 1
+#pragma unroll 4
       for (int q = grp; q < nq; q += R) {
         float a, vh, vl;
         get(col, q, a, vh, vl);
@@ -570,7 +570,7 @@ struct CtaSolver {
       c[u] = 0.f;
     }
     if (32 * warp >= m) return;  // no row of this warp is valid
-#pragma unroll 1
+#pragma unroll 4
     for (int k = 0; k < nv; ++k) {
       const float xh = vh[k], xl = vl[k];
 #pragma unroll
@@ -702,7 +702,7 @@ struct CtaSolver {
 #pragma unroll
     for (int u = 0; u < MTC; ++u) s_r[u] = 0.f;
     if (32 * warp < m) {  // warps without a valid row skip J p
-#pragma unroll 1
+#pragma unroll 4
       for (int k = 0; k < nv; ++k) {
         const float pk = vp[k];
 #pragma unroll
@@ -715,7 +715,7 @@ struct CtaSolver {
     if (tid < nv) {
       float mp = 0.f;
       const float* Mr = Mm + tid * MS;
-#pragma unroll 1
+#pragma unroll 4
       for (int k = 0; k < nv; ++k) mp = __fmaf_rn(Mr[k], vp[k], mp);
       pMp = vp[tid] * mp;
       c0 = vp[tid] * V(C_MAQ)[tid];
