@@ -161,13 +161,13 @@ struct CtaSolver {
     float* Ms_ = Ms();
     float* Js_ = Js();
     const int nc = geo.nvcap;
-#pragma unroll 1
+#pragma unroll 4
     for (int q = tid; q < nc * nc; q += kCtaThreads) {
       const int rr = q / nc, cc = q - rr * nc;
       Ms_[rr * geo.MS + cc] =
           (rr < nv && cc < nv) ? __ldg(M + rr * nv + cc) : (rr == cc ? 1.f : 0.f);
     }
-#pragma unroll 1
+#pragma unroll 4
     for (int q = tid; q < m * nv; q += kCtaThreads) {
       const int rr = q / nv, cc = q - rr * nv;
       Js_[rr * geo.JS + cc] = __ldg(J + q);
@@ -363,7 +363,7 @@ struct CtaSolver {
     for (int jb = 0; jb < 4; ++jb) {
       if (32 * jb >= nc) break;
       const int cend = min(32, nc - 32 * jb);
-#pragma unroll 1
+#pragma unroll 2
       for (int c0 = 0; c0 < cend; c0 += 4) {
         const int cb = 32 * jb + c0;
         float y[4];
@@ -395,7 +395,7 @@ struct CtaSolver {
     for (int jb = 3; jb >= 0; --jb) {
       if (32 * jb >= nc) continue;
       const int cend = min(32, nc - 32 * jb);
-#pragma unroll 1
+#pragma unroll 2
       for (int c0 = cend - 4; c0 >= 0; c0 -= 4) {
         const int ct = 32 * jb + c0;
         float z[4];
@@ -473,7 +473,7 @@ struct CtaSolver {
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll 1
+#pragma unroll 2
       for (int q = grp; q < nact; q += R) {
         const int i = idx[q];
         const float d = Dm[i];
