@@ -242,7 +242,7 @@ struct CtaElliptic {
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll 1
+#pragma unroll 2
       for (int q = grp; q < ncon; q += R) {
         const int r0 = idx[3 * q];
         const int c = r0 / 3;
@@ -322,7 +322,7 @@ struct CtaElliptic {
     if (tid < nv) {
       const float* Mr = S.Ms() + tid * S.geo.MS;
       float mp = 0.f;
-#pragma unroll 1
+#pragma unroll 4
       for (int k = 0; k < nv; ++k) mp = __fmaf_rn(Mr[k], vp[k], mp);
       pMp = vp[tid] * mp;
       two_prod(vp[tid], S.V(C_R)[tid], prh, prl);
