@@ -1098,6 +1098,29 @@ struct WarpSolver {
     return warp_max(df) <= kForceTol * fmax;
   }
 
+  // After a step a += alpha p that crossed no breakpoint: the residual
+  // quantities the adjoint and the outputs read (jar, the active forces f as
+  // a pair) advanced by alpha J p from the line search's products s_r = J p;
+  // the active set and its row list are unchanged.
+  __device__ __forceinline__ void advance_forces(float alpha) {
+    float* F = Fs();
+    float* Fl = Flo();
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+      if (row_valid(t)) {
+        const float ds = alpha * s_r[t];
+        jar_r[t] = __fadd_rn(jar_r[t], ds);
+        if ((act_bits >> t) & 1u) {
+          float fh = F[lane + 32 * t], fl = Fl[lane + 32 * t];
+          add_to_pair(fh, fl, D_r[t] * ds);
+          F[lane + 32 * t] = fh;
+          Fl[lane + 32 * t] = fl;
+        }
+      }
+    }
+    __syncwarp();
+  }
+
   // --------------------------------------------------------- forward solve
   // Newton iteration (Eqs. 9-10) from a0 = M^-1 qfrc (Eq. 1).  Returns the
   // status; *iters = Newton steps.  On return the residual quantities (jar,
@@ -1120,7 +1143,7 @@ struct WarpSolver {
     // conjugated (preconditioned CG, Fletcher-Reeves beta), restarted
     // whenever the active set or the factor changes.
     bool cg = false;
-    float p_prev = 0.f, zr_prev = 1.f;
+    float p_prev = 0.f, zr_prev = 1.f, dpm_prev = 0.f;
 #pragma unroll 1
     for (int k = 0;; ++k) {
       float scale;
@@ -1171,7 +1194,24 @@ struct WarpSolver {
       const float dp = alpha * p;
       add_to_pair(ah, al, dp);
       *iters = k + 1;
-      prev_small = precise && (warp_max(fabsf(dp)) <= kStepTol * amax) && (dfm <= kForceTol * fmax);
+      const float dpm = warp_max(fabsf(dp));
+      // A step at the settled set that crossed no breakpoint is a step of an
+      // iterative refinement (conjugated after the first): its steps shrink
+      // geometrically, by a ratio q estimated from two consecutive ones (the
+      // first against a itself; Demmel et al., ACM TOMS 32(2), 2006), so the
+      // error it leaves is about q / (1 - q) |dp|.  When that meets both
+      // stop tolerances the solve ends here, with f and jar advanced along
+      // the step instead of re-evaluated by another compensated residual.
+      if (precise && same && !crossed) {
+        const float q = dpm / (cg ? dpm_prev : amax);
+        const float gq = q / (1.f - q);
+        if (q < 0.5f && gq * dpm <= kStepTol * amax && gq * dfm <= kForceTol * fmax) {
+          advance_forces(alpha);
+          return CS_ST_OK;
+        }
+      }
+      dpm_prev = dpm;
+      prev_small = precise && (dpm <= kStepTol * amax) && (dfm <= kForceTol * fmax);
       prev_bits = act_bits;
       cg = precise && !crossed;
       p_prev = p;
@@ -1247,7 +1287,7 @@ struct WarpSolver {
   // compensated residuals.  Leaves w in (wh, wl), lambda = D_act . J w in
   // Lam() for every row < m.
   __device__ __forceinline__ void adjoint(float& wh, float& wl) {
-    solve_refined(gj, 0.f, wh, wl, kAdjStepTol, kAdjForceTol);
+    solve_refined<true>(gj, 0.f, wh, wl, kAdjStepTol, kAdjForceTol);
   }
 
   // H w = rhs + rhs_lo (spread per lane) with H = M + sum over the active
@@ -1263,6 +1303,16 @@ struct WarpSolver {
   // point that differs from w only beyond that resolution.  The default pair
   // is the forward's (FP32 resolution), which the unrolled reverse sweep
   // needs; the IFT adjoint passes the looser kAdjStepTol / kAdjForceTol.
+  //
+  // kPredict also ends the refinement one pass earlier: the corrections of
+  // an iterative refinement shrink geometrically, by a ratio q estimated from
+  // two consecutive ones (the first solve counting as the correction from
+  // w = 0; Demmel, Hida, Kahan, Li, Mukherjee and Riedy, "Error bounds from
+  // extra-precise iterative refinement", ACM TOMS 32(2), 2006), so the error
+  // left after applying dw is about q / (1 - q) |dw|.  When that meets both
+  // tolerances dw is applied, lambda advanced by D_act (J dw) from the
+  // products the test already formed, and no pass is spent confirming it.
+  template <bool kPredict = false>
   __device__ __forceinline__ void solve_refined(float rhs, float rhs_lo, float& wh, float& wl,
                                                 float step_tol = kStepTol,
                                                 float force_tol = kForceTol) {
@@ -1270,6 +1320,7 @@ struct WarpSolver {
     wl = 0.f;
     float* Lm = Lam();
     float* Lml = Lamlo();
+    float prev = 0.f;  // max |last correction| (0: w itself is the last one)
 #pragma unroll 1
     for (int it = 0;; ++it) {
       put_vec(V_WH, wh);
@@ -1320,6 +1371,22 @@ struct WarpSolver {
       dl = warp_max(dl);
       if (dmax <= step_tol * wmax && dl <= force_tol * lmax) break;
       add_to_pair(wh, wl, dw);
+      if (kPredict) {
+        const float q = dmax / (prev > 0.f ? prev : wmax);
+        const float gq = q / (1.f - q);
+        if (q < 0.5f && gq * dmax <= step_tol * wmax && gq * dl <= force_tol * lmax) {
+#pragma unroll
+          for (int t = 0; t < MT; ++t)
+            if ((act_bits >> t) & 1u) {
+              float lh = Lm[lane + 32 * t], ll = Lml[lane + 32 * t];
+              add_to_pair(lh, ll, D_r[t] * sd[t]);
+              Lm[lane + 32 * t] = lh;
+              Lml[lane + 32 * t] = ll;
+            }
+          break;
+        }
+        prev = dmax;
+      }
     }
     __syncwarp();
   }

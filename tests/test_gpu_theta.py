@@ -32,21 +32,25 @@ def test_theta_fused_and_split(cuda_device):
     f = parity.run_gpu_fused(batch, w, theta=True)
     _check(w, f, np.arange(w.n), "franka fused theta")
     masks = parity.valid_mask(w)
-    # with the kept factor the split path runs the fused path's arithmetic
-    # (bit for bit); recompute mode rebuilds the Newton matrix from M, where
-    # the forward formed it by row updates, so its gradients agree to the
-    # adjoint refinement's accuracy
+    # with the kept factor the split path runs the fused path's forward and
+    # adjoint solve (bit for bit); f and jar, which only dJ and dD read, may
+    # differ in their last bits (a fused solve that stops after a refinement
+    # step advances them along it, the split adjoint re-evaluates them).
+    # Recompute mode rebuilds the Newton matrix from M, where the forward
+    # formed it by row updates, so its gradients agree to the adjoint
+    # refinement's accuracy
     for keep in (True, False):
         s = parity.run_gpu_split(batch, w, keep_factor=keep, theta=True)
         for k in ("a", "dqfrc", "daref", "dJ", "dM", "dD", "status"):
             x = parity.valid(w, f, k, masks)
             y = parity.valid(w, s, k, masks)
-            if keep or k in ("a", "status"):
+            if k in ("a", "status") or (keep and k not in ("dJ", "dD")):
                 assert np.array_equal(x, y), (keep, k)
             else:
                 x = x.astype(np.float64)
                 y = y.astype(np.float64)
-                assert np.max(np.abs(x - y)) <= 1e-4 * max(np.max(np.abs(y)), 1e-30), (keep, k)
+                tol = 1e-6 if keep else 1e-4
+                assert np.max(np.abs(x - y)) <= tol * max(np.max(np.abs(y)), 1e-30), (keep, k)
 
 
 def test_theta_ragged_quadruped_and_tiny(cuda_device):
