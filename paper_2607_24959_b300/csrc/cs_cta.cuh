@@ -799,6 +799,28 @@ struct CtaSolver {
     return block_max(df) <= kForceTol * fmax;
   }
 
+  // After a step a += alpha p that crossed no breakpoint: jar and the active
+  // forces f (pair) advanced by alpha J p from the line search's products;
+  // the active set and its row list are unchanged (as in the warp solver).
+  __device__ __forceinline__ void advance_forces(float alpha) {
+    float* F = Fs();
+    float* Fl = Flo();
+#pragma unroll
+    for (int u = 0; u < MTC; ++u) {
+      if (row_valid(u)) {
+        const float ds = alpha * s_r[u];
+        jar_r[u] = __fadd_rn(jar_r[u], ds);
+        if ((act_bits >> u) & 1u) {
+          float fh = F[row(u)], fl = Fl[row(u)];
+          WarpSolver<1, 1>::add_to_pair(fh, fl, D_r[u] * ds);
+          F[row(u)] = fh;
+          Fl[row(u)] = fl;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
   __device__ __forceinline__ int forward(const Params& P, int* iters) {
     *iters = 0;
     if (!factor_M()) return CS_ST_CHOLFAIL;
@@ -815,7 +837,7 @@ struct CtaSolver {
     uint32_t prev_bits = 0;
     bool prev_small = false, precise = false;
     bool cg = false;  // conjugate settled-set steps (see the warp solver)
-    float zr_prev = 1.f;
+    float zr_prev = 1.f, smax_prev = 0.f;
     float* pp = V(C_PP);
 #pragma unroll 1
     for (int k = 0;; ++k) {
@@ -885,6 +907,16 @@ struct CtaSolver {
       }
       *iters = k + 1;
       const float smax = block_max(sm);
+      // predicted-error stop of the refinement steps (see the warp solver)
+      if (precise && same && !crossed) {
+        const float q = smax / (cg ? smax_prev : amax);
+        const float gq = (cg ? 1.f : kFirstRatioMargin) * q / (1.f - q);
+        if (q < 0.5f && gq * smax <= kStepTol * amax && gq * dfm <= kForceTol * fmax) {
+          advance_forces(alpha);
+          return CS_ST_OK;
+        }
+      }
+      smax_prev = smax;
       prev_small = precise && (smax <= kStepTol * amax) && (dfm <= kForceTol * fmax);
       prev_bits = act_bits;
       cg = precise && !crossed;
@@ -898,12 +930,17 @@ struct CtaSolver {
   // w = H^-1 (rhs + rhs_lo) for the factored H and the active list: a first
   // solve, then refinement with compensated residuals rhs - M w - J^T lambda
   // (lambda = D_act . (J w), compensated); stops when the untaken correction
-  // moves w by <= step_tol |w| and the active lambda by <= force_tol |lambda|.
+  // moves w by <= step_tol |w| and the active lambda by <= force_tol |lambda|,
+  // or (kPredict) once the correction just applied leaves a predicted error
+  // within them (geometric contraction, as in the warp solver; lambda is then
+  // advanced by D_act (J dw)).
   // Slots: rh / rl the right-hand side's parts (rl < 0: none), oh / ol the
   // result pair; jh / jl and mh / mr scratch (J^T lambda and M w pairs, mr
   // also the correction).  Leaves lambda (pair) in Lam() / Lamlo().
+  template <bool kPredict = false>
   __device__ __forceinline__ void solve_refined(int rh, int rl, int oh, int ol, int jh, int jl,
                                                 int mh, int mr, float step_tol, float force_tol) {
+    float prev = 0.f;  // max |last correction| (0: w itself is the last one)
     float* wh = V(oh);
     float* wl = V(ol);
     for (int j = tid; j < geo.nvcap; j += kCtaThreads) {
@@ -981,14 +1018,31 @@ struct CtaSolver {
       }
       const float dmax = block_max(dm);
       const float wmax = block_max(wm);
-      if (dmax <= step_tol * wmax) {
+      const float q = dmax / (prev > 0.f ? prev : wmax);
+      const float gq = (prev > 0.f ? 1.f : kFirstRatioMargin) * q / (1.f - q);
+      const bool predict = kPredict && q < 0.5f && gq * dmax <= step_tol * wmax;
+      bool done = false;
+      if (dmax <= step_tol * wmax || predict) {
         float sd[MTC], cd[MTC];
         rows_dot(rho, rho, false, sd, cd);
         float dl = 0.f;
 #pragma unroll
         for (int u = 0; u < MTC; ++u)
           if ((act_bits >> u) & 1u) dl = fmaxf(dl, fabsf(D_r[u] * sd[u]));
-        if (block_max(dl) <= force_tol * lmax) break;
+        dl = block_max(dl);
+        if (dmax <= step_tol * wmax && dl <= force_tol * lmax) break;
+        if (predict && gq * dl <= force_tol * lmax) {
+          // apply dw and advance lambda by D_act (J dw) (own rows only)
+#pragma unroll
+          for (int u = 0; u < MTC; ++u)
+            if ((act_bits >> u) & 1u) {
+              float lh = Lm[row(u)], ll = Lamlo()[row(u)];
+              WarpSolver<1, 1>::add_to_pair(lh, ll, D_r[u] * sd[u]);
+              Lm[row(u)] = lh;
+              Lamlo()[row(u)] = ll;
+            }
+          done = true;
+        }
       }
       if (tid < nv) {
         float hh = wh[tid], ll = wl[tid];
@@ -997,6 +1051,8 @@ struct CtaSolver {
         wl[tid] = ll;
       }
       __syncthreads();
+      if (done) break;
+      prev = dmax;
     }
     __syncthreads();
   }
@@ -1005,7 +1061,7 @@ struct CtaSolver {
   // refined to the adjoint's resolution (kAdjStepTol, kAdjForceTol, as in
   // the warp solver).
   __device__ __forceinline__ void adjoint() {
-    solve_refined(C_G, -1, C_WH, C_WL, C_X, C_MP, C_P, C_R, kAdjStepTol, kAdjForceTol);
+    solve_refined<true>(C_G, -1, C_WH, C_WL, C_X, C_MP, C_P, C_R, kAdjStepTol, kAdjForceTol);
   }
 
   // Active list and bits from a given row mask (rows in order).

@@ -445,6 +445,7 @@ struct CtaElliptic {
 #pragma unroll
     for (int k = 0; k < 3 * MCTC; ++k) lam_prev[k] = 0.f;
     float dmax_prev = CUDART_INF_F;
+    float dmax_pp = 0.f;  // the correction before dmax_prev (0: w itself)
 #pragma unroll 1
     for (int it = 0; it <= it_max; ++it) {
       rows_to_smem(wh, wl, false, Xh(), Xl());
@@ -484,7 +485,17 @@ struct CtaElliptic {
       dl = S.block_max(dl);
       if (it > 0) {
         const float wmax = S.block_max(tid < nv ? fabsf(wh[tid]) : 0.f);
-        if ((dmax_prev <= step_tol * wmax && dl <= force_tol * lmax) || it == it_max) break;
+        // or the error left after the correction just applied, predicted
+        // from the contraction of two consecutive ones (see the warp
+        // solver's refinement), meets both tolerances
+        const float q = dmax_prev / (dmax_pp > 0.f ? dmax_pp : wmax);
+        const float gq = (dmax_pp > 0.f ? 1.f : kFirstRatioMargin) * q / (1.f - q);
+        const bool predicted = q < 0.5f && gq * dmax_prev <= step_tol * wmax &&
+                               gq * dl <= force_tol * lmax;
+        if ((dmax_prev <= step_tol * wmax && dl <= force_tol * lmax) || predicted ||
+            it == it_max)
+          break;
+        dmax_pp = dmax_prev;
       }
       S.split_dot(nv, S.nact, true,
                   [&](int j, int q, float& a, float& h, float& l) {
@@ -543,6 +554,7 @@ struct CtaElliptic {
     uint32_t prev_z = 0;
     bool prev_small = false;
     int stall = 0;
+    float smax_prev = 0.f;
 #pragma unroll 1
     for (int k = 0;; ++k) {
       float scale;
@@ -582,7 +594,13 @@ struct CtaElliptic {
       }
       *iters = k + 1;
       const float smax = S.block_max(sm);  // also orders the updates of a
-      prev_small = (smax <= kStepTol * amax) && (dfm <= kForceTol * S.fmax);
+      // small, or predicted small (as in the warp kernel)
+      const float q = smax / smax_prev;
+      const float gq = q / (1.f - q);
+      const bool predicted = same && smax_prev > 0.f && q < 0.5f &&
+                             gq * smax <= kStepTol * amax && gq * dfm <= kForceTol * S.fmax;
+      prev_small = ((smax <= kStepTol * amax) && (dfm <= kForceTol * S.fmax)) || predicted;
+      smax_prev = smax;
       stall = (smax <= kStepTol * amax && same) ? stall + 1 : 0;
       prev_z = zbits;
     }

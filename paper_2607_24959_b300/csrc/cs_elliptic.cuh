@@ -503,6 +503,7 @@ struct EllipticSolver {
 #pragma unroll
     for (int k = 0; k < 3 * E::MCT; ++k) lam_prev[k] = 0.f;
     float dmax_prev = CUDART_INF_F;
+    float dmax_pp = 0.f;  // the correction before dmax_prev (0: w itself)
 #pragma unroll 1
     for (int it = 0; it <= it_max; ++it) {
       S.put_vec(V_WH, wh);
@@ -547,7 +548,17 @@ struct EllipticSolver {
       __syncwarp();
       if (it > 0) {
         const float wmax = warp_max(fabsf(wh));
-        if ((dmax_prev <= step_tol * wmax && dl <= force_tol * lmax) || it == it_max) break;
+        // or the error left after the correction just applied, predicted
+        // from the contraction of two consecutive ones (see the warp
+        // solver's refinement), meets both tolerances
+        const float q = dmax_prev / (dmax_pp > 0.f ? dmax_pp : wmax);
+        const float gq = (dmax_pp > 0.f ? 1.f : kFirstRatioMargin) * q / (1.f - q);
+        const bool predicted = q < 0.5f && gq * dmax_prev <= step_tol * wmax &&
+                               gq * dl <= force_tol * lmax;
+        if ((dmax_prev <= step_tol * wmax && dl <= force_tol * lmax) || predicted ||
+            it == it_max)
+          break;
+        dmax_pp = dmax_prev;
       }
       float js, jc, ms, mc;
       S.jt_active(Lm, Lml, js, jc);
@@ -573,6 +584,7 @@ struct EllipticSolver {
     uint32_t prev_z = 0;
     bool prev_small = false;
     int stall = 0;
+    float smax_prev = 0.f;
 #pragma unroll 1
     for (int k = 0;; ++k) {
       float scale;
@@ -609,7 +621,16 @@ struct EllipticSolver {
       WarpSolver<NV, MT>::add_to_pair(S.ah, S.al, dp);
       *iters = k + 1;
       const float smax = warp_max(fabsf(dp));
-      prev_small = (smax <= kStepTol * amax) && (dfm <= kForceTol * S.fmax);
+      // the step is small, or (two consecutive steps in the same zones) the
+      // error it leaves, predicted from their contraction ratio q as q / (1 -
+      // q) |dp| (conservative where Newton converges quadratically), is; the
+      // residual at the new point is still evaluated before returning
+      const float q = smax / smax_prev;
+      const float gq = q / (1.f - q);
+      const bool predicted = same && smax_prev > 0.f && q < 0.5f &&
+                             gq * smax <= kStepTol * amax && gq * dfm <= kForceTol * S.fmax;
+      prev_small = ((smax <= kStepTol * amax) && (dfm <= kForceTol * S.fmax)) || predicted;
+      smax_prev = smax;
       stall = (smax <= kStepTol * amax && same) ? stall + 1 : 0;
       prev_z = zbits;
     }

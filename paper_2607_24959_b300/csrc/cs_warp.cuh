@@ -45,6 +45,11 @@ constexpr int kAdjointRefineMax = 8;
 // refinement iteration has reached its attainable accuracy.
 constexpr float kStepTol = 1.0e-7f;
 constexpr float kForceTol = 1.0e-6f;
+// Margin on the predicted-error stop of the refinement steps when the
+// contraction ratio comes from the first correction alone (measured against
+// the solution itself, which tracks the true ratio only loosely at large
+// cond(H)); a ratio of two consecutive corrections is used as it is.
+constexpr float kFirstRatioMargin = 16.0f;
 // The adjoint's refinement stops once the next correction would move w by
 // <= kAdjStepTol |w| and the active lambda = D_act . J w by <= kAdjForceTol
 // |lambda|: that bounds the remaining error of every gradient well below the
@@ -1204,7 +1209,7 @@ struct WarpSolver {
       // the step instead of re-evaluated by another compensated residual.
       if (precise && same && !crossed) {
         const float q = dpm / (cg ? dpm_prev : amax);
-        const float gq = q / (1.f - q);
+        const float gq = (cg ? 1.f : kFirstRatioMargin) * q / (1.f - q);
         if (q < 0.5f && gq * dpm <= kStepTol * amax && gq * dfm <= kForceTol * fmax) {
           advance_forces(alpha);
           return CS_ST_OK;
@@ -1373,7 +1378,7 @@ struct WarpSolver {
       add_to_pair(wh, wl, dw);
       if (kPredict) {
         const float q = dmax / (prev > 0.f ? prev : wmax);
-        const float gq = q / (1.f - q);
+        const float gq = (prev > 0.f ? 1.f : kFirstRatioMargin) * q / (1.f - q);
         if (q < 0.5f && gq * dmax <= step_tol * wmax && gq * dl <= force_tol * lmax) {
 #pragma unroll
           for (int t = 0; t < MT; ++t)
