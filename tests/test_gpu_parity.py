@@ -61,6 +61,40 @@ def test_quadruped_full_size_sampled(cuda_device):
     _check(w, gpu, idx, "quadruped-32768 fused (sampled)")
 
 
+@pytest.mark.parametrize("name,extra_steps", [("quadruped", 1.25), ("franka", 0.75), ("nv96", 3.0)])
+def test_newton_steps_and_accuracy_against_the_oracle(cuda_device, name, extra_steps):
+    """The GPU takes the oracle's Newton steps plus the refinement steps the
+    FP32 contract costs (the oracle ends on exact termination after the step
+    that keeps the active set; in FP32 that step leaves a with the error of
+    an FP32 solve, removed by one refinement step, two to three at cond(M)
+    1e4), and returns a near FP32 resolution and gradients near 1e-5: far
+    inside the parity tolerances, which a looser stop rule would still meet."""
+    gen = {"quadruped": lambda: W.quadruped(n=2048, seed=81),
+           "franka": lambda: W.franka(n=2048, seed=82),
+           "nv96": lambda: W.nv96(n=192, seed=83)}[name]
+    w = gen()
+    batch = solver.DeviceBatch.from_workload(w, cuda_device)
+    gpu = parity.run_gpu_fused(batch, w)
+    ref = oracle.solve_workload(w, threads=8)
+    ok = (gpu["status"][:w.n] == 0) & (ref["status"][:w.n] == 0)
+    assert ok.mean() > 0.99
+    g_it = gpu["iters"][:w.n][ok].mean()
+    o_it = ref["iters"][:w.n][ok].mean()
+    print(f"{name}: GPU {g_it:.2f} Newton steps per solve, oracle {o_it:.2f}")
+    assert g_it <= o_it + extra_steps, (g_it, o_it)
+    worst_a = worst_g = 0.0
+    for b in np.flatnonzero(ok):
+        e = w.inst[b]
+        nv, m = int(e["nv"]), int(e["m"])
+        ov, orr, oJ = int(e["off_v"]), int(e["off_r"]), int(e["off_J"])
+        worst_a = max(worst_a, parity.rel(gpu["a"][ov:ov + nv], ref["a"][ov:ov + nv]))
+        for k, sl in (("dqfrc", slice(ov, ov + nv)), ("daref", slice(orr, orr + m)),
+                      ("dJ", slice(oJ, oJ + m * nv))):
+            worst_g = max(worst_g, parity.rel(gpu[k][sl], ref[k][sl]))
+    print(f"{name}: worst relative error a {worst_a:.2e}, gradients {worst_g:.2e}")
+    assert worst_a <= 5e-6 and worst_g <= 2e-4, (worst_a, worst_g)
+
+
 def test_fused_equals_split_bitwise(cuda_device):
     """The fused kernel and the split forward + adjoint with the kept factor
     share the forward and the adjoint solve bit for bit (a, status, iters, w =
