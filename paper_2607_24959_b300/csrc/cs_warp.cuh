@@ -508,6 +508,10 @@ struct WarpSolver {
   // column-at-a-time substitution, so the result is identical bit for bit;
   // the dependency chain has one shuffle per block instead of per column.
   static constexpr int kSB = (NV % 4 == 0) ? 4 : (NV % 3 == 0) ? 3 : (NV % 2 == 0) ? 2 : 1;
+  // Block rounds unrolled in full only for small NV: at NV = 9 that took the
+  // Franka step from 0.176 to 0.171 ms; at NV = 18 the unrolled copies (one
+  // per call site) made the quadruped step 12 % slower.
+  static constexpr int kSubUnroll = (NV <= 9) ? NV / kSB : 1;
   __device__ __forceinline__ float chol_solve(float x) { return chol_backward(chol_forward(x)); }
 
   // L y = x (forward substitution, blocked as above).
@@ -515,7 +519,7 @@ struct WarpSolver {
     const float* L = Ls();
     const float* dinv = Vec(V_DINV);
     const float* Lrow = L + min(lane, NV - 1) * G::MS;
-#pragma unroll 1
+#pragma unroll (kSubUnroll)
     for (int kb = 0; kb < NV; kb += kSB) {
       float y[kSB];
 #pragma unroll
@@ -542,7 +546,7 @@ struct WarpSolver {
   __device__ __forceinline__ float chol_backward(float x) {
     const float* L = Ls();
     const float* dinv = Vec(V_DINV);
-#pragma unroll 1
+#pragma unroll (kSubUnroll)
     for (int kt = NV - kSB; kt >= 0; kt -= kSB) {
       float z[kSB];
 #pragma unroll
@@ -776,6 +780,36 @@ struct WarpSolver {
     }
   }
 
+  // Transposed products over the active rows.  From NV = 16 on the lanes
+  // take (column pair, row group): lane l reads columns 2 (l % NP) and
+  // 2 (l % NP) + 1 of J with one 8-byte load, for every kTG-th active row
+  // from l / NP on (kTG = 32 / NP groups: 3 at NV = 18, 2 at NV = 32); the
+  // groups' partial sums meet in the lanes of group 0 by shuffles, and lane j
+  // then takes column j from lane j / 2.  Below NV = 16 lane j walks column
+  // j over every active row.
+  static constexpr int kTG = 32 / G::NP;
+
+  // Group 0's lanes gather the partial sums of the other groups (shuffled
+  // from copies, so that no lane reads a sum another lane already added to).
+  __device__ __forceinline__ static void gather_groups(float& x, int lane) {
+    const float o = x;
+#pragma unroll
+    for (int g = 1; g < kTG; ++g) x += __shfl_sync(kFull, o, lane + g * G::NP);
+  }
+  __device__ __forceinline__ static void gather_groups(float& s, float& c, int lane) {
+    const float os = s, oc = c;
+#pragma unroll
+    for (int g = 1; g < kTG; ++g)
+      add_pair(s, c, __shfl_sync(kFull, os, lane + g * G::NP),
+               __shfl_sync(kFull, oc, lane + g * G::NP));
+  }
+  // Column j of a pair-spread result, for lane j (0 beyond NV).
+  __device__ __forceinline__ float column_of_pairs(float x, float y) const {
+    const float ex = __shfl_sync(kFull, x, lane >> 1);
+    const float ey = __shfl_sync(kFull, y, lane >> 1);
+    return (lane < NV) ? ((lane & 1) ? ey : ex) : 0.f;
+  }
+
   // (s, c) = sum over active rows i of J_ij (v_i + vlo_i), for lane j
   // (compensated; v carried as a float pair so that a force computed from a
   // rounded jar does not put a floor under the residual).
@@ -783,6 +817,30 @@ struct WarpSolver {
                                             float& c) {
     const float* Jm = Js();
     const idx_t* idx = Idx();
+    if constexpr (NV >= 16) {
+      constexpr int RS = G::JS / 2;  // J row stride in float2
+      const int gg = lane / G::NP;
+      const float2* Jp = reinterpret_cast<const float2*>(Jm) + lane % G::NP;
+      // one row per pass: the two compensated chains already hide each
+      // other's latency, and a second pair of them measured slower (register
+      // pressure)
+      float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+      if (gg < kTG) {
+#pragma unroll 1
+        for (int q = gg; q < nact; q += kTG) {
+          const int i0 = idx[q];
+          const float2 a = Jp[i0 * RS];
+          const float h0 = v[i0], l0 = vlo[i0];
+          dot2(sx, cx, a.x, h0, l0);
+          dot2(sy, cy, a.y, h0, l0);
+        }
+      }
+      gather_groups(sx, cx, lane);
+      gather_groups(sy, cy, lane);
+      s = column_of_pairs(sx, sy);
+      c = column_of_pairs(cx, cy);
+      return;
+    }
     float s2 = 0.f, c2 = 0.f;
     s = 0.f;
     c = 0.f;
@@ -861,6 +919,36 @@ struct WarpSolver {
   __device__ __forceinline__ float jt_active_plain(const float* v) {
     const float* Jm = Js();
     const idx_t* idx = Idx();
+    if constexpr (NV >= 16) {
+      constexpr int RS = G::JS / 2;
+      const int gg = lane / G::NP;
+      const float2* Jp = reinterpret_cast<const float2*>(Jm) + lane % G::NP;
+      float sx = 0.f, sy = 0.f, tx = 0.f, ty = 0.f;
+      if (gg < kTG) {
+        int q = gg;
+#pragma unroll 1
+        for (; q + kTG < nact; q += 2 * kTG) {
+          const int i0 = idx[q], i1 = idx[q + kTG];
+          const float2 a = Jp[i0 * RS], b = Jp[i1 * RS];
+          const float v0 = v[i0], v1 = v[i1];
+          sx = __fmaf_rn(a.x, v0, sx);
+          sy = __fmaf_rn(a.y, v0, sy);
+          tx = __fmaf_rn(b.x, v1, tx);
+          ty = __fmaf_rn(b.y, v1, ty);
+        }
+        if (q < nact) {
+          const int i0 = idx[q];
+          const float2 a = Jp[i0 * RS];
+          sx = __fmaf_rn(a.x, v[i0], sx);
+          sy = __fmaf_rn(a.y, v[i0], sy);
+        }
+      }
+      sx += tx;
+      sy += ty;
+      gather_groups(sx, lane);
+      gather_groups(sy, lane);
+      return column_of_pairs(sx, sy);
+    }
     float s = 0.f, s2 = 0.f;
     if (lane < NV) {
       int q = 0;
@@ -929,17 +1017,28 @@ struct WarpSolver {
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
       if (32 * t < m) {
-        float u, ue;
-        two_sum(s[t], -aref_r[t], u, ue);
-        const float tl = __fadd_rn(ue, c[t]);
-        jar_r[t] = __fadd_rn(u, tl);
-        const float jlo = __fsub_rn(tl, __fsub_rn(jar_r[t], u));
+        // plain: jar = fl(s - aref) and f = fl(D jar), the high parts of the
+        // compensated forms; f's low part is read only after a compensated
+        // residual has rewritten it
+        float jlo = 0.f;
+        if (precise) {
+          float u, ue;
+          two_sum(s[t], -aref_r[t], u, ue);
+          const float tl = __fadd_rn(ue, c[t]);
+          jar_r[t] = __fadd_rn(u, tl);
+          jlo = __fsub_rn(tl, __fsub_rn(jar_r[t], u));
+        } else {
+          jar_r[t] = __fsub_rn(s[t], aref_r[t]);
+        }
         const bool on = row_valid(t) && jar_r[t] < 0.f;
         float f = 0.f, flo = 0.f;
-        if (on) scale_pair(D_r[t], jar_r[t], jlo, f, flo);
+        if (on) {
+          if (precise) scale_pair(D_r[t], jar_r[t], jlo, f, flo);
+          else f = __fmul_rn(D_r[t], jar_r[t]);
+        }
         if (row_valid(t)) {
           F[lane + 32 * t] = f;
-          Fl[lane + 32 * t] = flo;
+          if (precise) Fl[lane + 32 * t] = flo;
         }
         fm = fmaxf(fm, fabsf(f));
         const unsigned bal = __ballot_sync(kFull, on);
@@ -1052,11 +1151,11 @@ struct WarpSolver {
         x0 = an;
         x1 = alpha;
       }
-      int cnt = 0;
+      // any breakpoint strictly between the trial and its Newton point
+      bool inside = false;
 #pragma unroll
-      for (int t = 0; t < MT; ++t)
-        cnt += __popc(__ballot_sync(kFull, bp[t] > x0 && bp[t] < x1));
-      if (cnt == 0 && an > 0.f) {
+      for (int t = 0; t < MT; ++t) inside = inside || (bp[t] > x0 && bp[t] < x1);
+      if (!__any_sync(kFull, inside) && an > 0.f) {
         alpha = an;
         break;
       }
