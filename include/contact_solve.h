@@ -142,7 +142,20 @@ const char* cs_last_error(void);
 
 /* Forward solve (Eqs. 1, 5-10).  Writes a (device, total_v) and the adjoint
  * state.  Returns CS_EINVAL for a NULL/inconsistent argument, CS_ECUDA on a
- * launch failure. */
+ * launch failure.
+ *
+ * Accuracy and stopping (FP32 with compensated residuals): an instance
+ * returns CS_ST_OK when ||r|| <= tol * scale, or, once its active set has
+ * settled, when the Newton correction it would take next, or the error the
+ * refinement step just taken is predicted to leave (from the ratio of
+ * consecutive corrections), is within 1e-7 max|a| and moves no active force
+ * by more than 1e-6 max|f|.  a then lies within about 1e-6 (relative, max
+ * norm) of the exact minimiser; the adjoints refine w to 1e-5 and lambda to
+ * 3e-5 the same way.  The forces f behind dJ and dD are the forward's own in
+ * cs_solve_fused, re-evaluated at the returned a in cs_solve_adjoint: with
+ * keep_factor == 1 the two paths agree bit for bit in a, dqfrc and daref and
+ * to rounding in dJ and dD (with keep_factor == 0, a agrees bit for bit and
+ * the gradients to the refinement's accuracy). */
 int cs_solve_fwd(const cs_batch* batch, const cs_options* opt, float* a,
                  const cs_state* state, void* stream);
 
