@@ -377,6 +377,8 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
     # collect exactly the tickets the server reports as completed (no scan
     # of the outstanding ones under the server's lock)
     t_done = np.zeros(n)
+    t_sub = np.zeros(n)
+    t_start = np.zeros(n)
     status = np.full(n, -1, np.int64)
     comp = (ctypes.c_uint64 * 8192)()
     rtmp = (_lib.CsResult * 8192)()
@@ -395,6 +397,8 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
                     raise RuntimeError("serving lost a ticket")
                 idx = int(comp[i]) - int(tickets[0])   # tickets are consecutive
                 t_done[idx] = rtmp[i].t_done
+                t_sub[idx] = rtmp[i].t_submit
+                t_start[idx] = rtmp[i].t_start
                 status[idx] = rtmp[i].status
             collected += k
         else:
@@ -408,8 +412,19 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
     srv.close()
     lat = t_done - (t0 + np.asarray(t_arr))
     span = t_done.max() - (t0 + t_arr[0])
+    # where the latency goes: the client's lag behind the scheduled arrival,
+    # the wait in the server's queue, and the batch's GPU round trip
+    # (staging, copies, kernels, completion), medians and 99th percentiles
+    parts = {"client_lag": t_sub - (t0 + np.asarray(t_arr)), "queue": t_start - t_sub,
+             "service": t_done - t_start}
+    split = {k: {"p50_ms": float(np.percentile(v, 50) * 1e3),
+                 "p99_ms": float(np.percentile(v, 99) * 1e3)} for k, v in parts.items()}
+    nvs = np.array([len(r["qfrc"]) for r in reqs])
+    split["by_nv"] = {int(v): {"p50_ms": float(np.percentile(lat[nvs == v], 50) * 1e3),
+                               "p99_ms": float(np.percentile(lat[nvs == v], 99) * 1e3)}
+                      for v in np.unique(nvs)}
     return {"requests": n, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "latency_split": split,
             "mean_ms": float(lat.mean() * 1e3), "solves_per_s": n / span,
             "ok": int(np.sum(status == 0)), "batches": int(st["batches"]),
             "mean_batch": st["batched_requests"] / max(st["batches"], 1),

@@ -88,6 +88,9 @@ struct CudaBackend {
   bool record(void* ev, void* s) {
     return cudaEventRecord((cudaEvent_t)ev, (cudaStream_t)s) == cudaSuccess;
   }
+  bool wait_event(void* s, void* ev) {
+    return cudaStreamWaitEvent((cudaStream_t)s, (cudaEvent_t)ev, 0) == cudaSuccess;
+  }
   int query(void* ev) {
     const cudaError_t q = cudaEventQuery((cudaEvent_t)ev);
     return q == cudaSuccess ? 0 : q == cudaErrorNotReady ? 1 : -1;

@@ -137,9 +137,17 @@ struct LaunchDesc {
   int32_t max_iter = 0;
 };
 
+// Auxiliary streams per slot: a batch's bucket kernels run side by side,
+// the first on the slot's stream and the others on these, so that a batch
+// waits for its slowest bucket rather than for the sum of them.
+constexpr int kAuxStreams = 3;
+
 struct Slot {
   void* stream = nullptr;
   void* done = nullptr;
+  void* aux[kAuxStreams] = {};   // bucket streams besides `stream`
+  void* fork = nullptr;          // recorded on `stream` after the upload
+  void* join[kAuxStreams] = {};  // recorded on aux[a] after its kernels
   char* d = nullptr;  // device region
   char* h = nullptr;  // pinned staging, same layout
   size_t cap = 0;
@@ -161,6 +169,7 @@ struct Slot {
 //   bool d2h(void* dst, const void* src, size_t, void* stream);
 //   bool launch(const LaunchDesc&, void* stream);
 //   bool record(void* event, void* stream);
+//   bool wait_event(void* stream, void* event);  // stream waits for event
 //   int query(void* event);     // 0 done, 1 not yet, -1 failed
 //   void sync(void* stream);
 //   bool warp_sized(int nv, int m);          // one warp solves it (else a CTA)
@@ -219,7 +228,9 @@ struct Server {
       sl.cap = per;
       sl.d = d_arena + (size_t)i * per;
       ok = be.stream_create(&sl.stream) && be.event_create(&sl.done) &&
-           be.alloc_pinned(per, &sl.h);
+           be.event_create(&sl.fork) && be.alloc_pinned(per, &sl.h);
+      for (int a = 0; a < kAuxStreams && ok; ++a)
+        ok = be.stream_create(&sl.aux[a]) && be.event_create(&sl.join[a]);
     }
     if (!ok) {
       release();
@@ -234,8 +245,14 @@ struct Server {
       if (sl.h) be.free_pinned(sl.h);
       if (sl.stream) be.stream_destroy(sl.stream);
       if (sl.done) be.event_destroy(sl.done);
+      if (sl.fork) be.event_destroy(sl.fork);
+      for (int a = 0; a < kAuxStreams; ++a) {
+        if (sl.aux[a]) be.stream_destroy(sl.aux[a]);
+        if (sl.join[a]) be.event_destroy(sl.join[a]);
+        sl.aux[a] = sl.join[a] = nullptr;
+      }
       sl.h = nullptr;
-      sl.stream = sl.done = nullptr;
+      sl.stream = sl.done = sl.fork = nullptr;
     }
     if (d_arena) be.free_device(d_arena);
     d_arena = nullptr;
@@ -248,9 +265,15 @@ struct Server {
     }
     cv.notify_one();
     if (worker.joinable()) worker.join();
-    for (auto& sl : slots)
-      if (sl.stream) be.sync(sl.stream);
+    for (auto& sl : slots) sync_slot(sl);
     release();
+  }
+
+  // Wait for everything a slot's batch issued, on all of its streams.
+  void sync_slot(Slot& sl) {
+    if (sl.stream) be.sync(sl.stream);
+    for (int a = 0; a < kAuxStreams; ++a)
+      if (sl.aux[a]) be.sync(sl.aux[a]);
   }
 
   // A fault hook step fails when the hook returns nonzero.
@@ -377,6 +400,14 @@ struct Server {
     L.iters = reinterpret_cast<int32_t*>(dout + out_floats) + sl.o_it;
     L.tol = cfg.tol;
     L.max_iter = cfg.max_iter;
+    // bucket 0 on the slot's stream, bucket b > 0 on aux[(b - 1) % kAux],
+    // forked after the upload and joined before the download
+    const int n_aux = std::min((int)groups.size() - 1, kAuxStreams);
+    if (n_aux > 0) {
+      if (!be.record(sl.fork, sl.stream)) return false;
+      for (int a = 0; a < n_aux; ++a)
+        if (!be.wait_event(sl.aux[a], sl.fork)) return false;
+    }
     int bi = 0, pos = 0;
     for (auto& kv : groups) {
       LaunchDesc Q = L;
@@ -387,9 +418,13 @@ struct Server {
       Q.nv_max = maxima[kv.first].first;
       Q.m_max = maxima[kv.first].second;
       pos += Q.n_work;
-      if (injected(CS_SERVE_FAULT_LAUNCH, sl.seq) || !be.launch(Q, sl.stream)) return false;
+      void* s = bi == 0 ? sl.stream : sl.aux[(bi - 1) % kAuxStreams];
+      if (injected(CS_SERVE_FAULT_LAUNCH, sl.seq) || !be.launch(Q, s)) return false;
       ++bi;
     }
+    for (int a = 0; a < n_aux; ++a)
+      if (!be.record(sl.join[a], sl.aux[a]) || !be.wait_event(sl.stream, sl.join[a]))
+        return false;
     if (injected(CS_SERVE_FAULT_D2H, sl.seq) ||
         !be.d2h(sl.h + sl.out_off, sl.d + sl.out_off, sl.out_bytes, sl.stream))
       return false;
@@ -471,7 +506,7 @@ struct Server {
         lk.unlock();
         if (q != 0) {
           failed_launches++;
-          be.sync(sl.stream);
+          sync_slot(sl);
         }
         finish_slot(sl, q == 0);
         lk.lock();
@@ -535,7 +570,7 @@ struct Server {
         const bool ok = launch_slot(sl);
         if (!ok) {
           failed_launches++;
-          be.sync(sl.stream);
+          sync_slot(sl);
           finish_slot(sl, false);
         }
         lk.lock();
