@@ -437,7 +437,7 @@ def run_serve(args):
     a sweep of the arrival rate (the same mix, fewer requests per rate above
     the headline one) to find where each policy stops keeping up."""
     t_arr, reqs = _serve_pool(args.serve_requests, args.serve_rate, 1005)
-    cont = serve_run(t_arr, reqs, "continuous")
+    cont = serve_run(t_arr, reqs, "continuous", streams=args.serve_streams)
     fixed = serve_run(t_arr, reqs, "fixed", fixed_batch=args.serve_fixed_batch)
     out = {"requests": args.serve_requests, "rate_per_s": args.serve_rate,
            "mix": "nv {3,9,18,96} p {.3,.3,.3,.1}, nc U{0..64}, fwd + adjoint each",
@@ -448,7 +448,8 @@ def run_serve(args):
         t_s, r_s = _serve_pool(n, rate, 1005)
         row = {"rate_per_s": rate, "requests": n}
         for pol in ("continuous", "fixed"):
-            res = serve_run(t_s, r_s, pol, fixed_batch=args.serve_fixed_batch)
+            res = serve_run(t_s, r_s, pol, fixed_batch=args.serve_fixed_batch,
+                            streams=args.serve_streams)
             row[pol] = {k: res[k] for k in ("p50_ms", "p99_ms", "solves_per_s", "ok",
                                             "mean_batch", "max_inflight")}
         sweep.append(row)
@@ -1027,6 +1028,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200000)
     ap.add_argument("--serve-rate", type=float, default=50000.0)
     ap.add_argument("--serve-fixed-batch", type=int, default=1024)
+    ap.add_argument("--serve-streams", type=int, default=8,
+                    help="batches in flight at once for the continuous policy (1..16)")
     ap.add_argument("--serve-sweep", default="200000,500000,1000000",
                     help="arrival rates (req/s) of the serving sweep; empty to skip")
     args = ap.parse_args()
