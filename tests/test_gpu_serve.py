@@ -153,3 +153,40 @@ def test_host_injected_launch_failure_on_the_gpu_server(cuda_device):
     assert [r["status"] for r in res] == [0] * 4 + [_lib.ST_FAILED] * 4 + [0] * 4
     assert all(not np.any(r["a"]) for r in res[4:8])
     assert st["failed_launches"] == 1 and st["batches"] == 3
+
+
+def test_failure_after_some_bucket_kernels_were_launched(cuda_device):
+    """A batch's four bucket kernels run on the slot's stream and its three
+    auxiliary streams.  The third launch of batch 1 is made to fail on the
+    host after the first two were issued: exactly that batch completes with
+    CS_ST_FAILED, the slot is waited for on all of its streams and reused at
+    once (one slot), and the next batch on it gives the results the same
+    requests give alone."""
+    from paper_2607_24959_b300 import _lib
+    sizes = [(3, 2), (9, 10), (18, 20), (18, 40)]   # four (nv, rows) buckets
+    reqs = [W.serve_request(100 + 4 * w + k, nv, nc, seed=72)
+            for w in range(3) for k, (nv, nc) in enumerate(sizes)]
+    calls = []
+
+    def hook(stage, batch):
+        if stage == _lib.SERVE_FAULT_LAUNCH and batch == 1:
+            calls.append(1)
+            return len(calls) == 3
+        return False
+
+    with serve.Server(arena_bytes=256 << 20, streams=1, policy="fixed",
+                      fixed_batch=4) as srv:
+        srv.set_fault_hook(hook)
+        res = []
+        for w in range(3):
+            res += _wait(srv, [_submit(srv, p) for p in reqs[4 * w:4 * w + 4]])
+        st = srv.stats()
+        srv.set_fault_hook(None)
+    assert len(calls) == 3
+    assert [r["status"] for r in res] == [0] * 4 + [_lib.ST_FAILED] * 4 + [0] * 4
+    assert st["failed_launches"] == 1 and st["batches"] == 3
+    with serve.Server(arena_bytes=256 << 20, streams=1) as srv:
+        alone = [_wait(srv, [_submit(srv, p)])[0] for p in reqs[8:]]
+    for a, b in zip(alone, res[8:]):
+        for k in ("a", "dqfrc", "daref", "dJ"):
+            assert np.array_equal(a[k], b[k]), k

@@ -156,6 +156,38 @@ def test_injected_failure_fails_exactly_that_batch(fake, stage):
         srv.close()
 
 
+def test_failure_after_some_bucket_launches(fake):
+    """A batch's bucket kernels are forked over the slot's stream and its
+    auxiliary streams; a launch that fails after two of the batch's four
+    bucket launches were issued fails exactly that batch, and the slot is
+    reused by the next one."""
+    rng = np.random.default_rng(11)
+    srv = FakeServer(fake, fixed_batch=4, streams=1)
+    sizes = [(6, 8), (6, 300), (40, 8), (40, 300)]   # four buckets of the fake device
+    calls = []
+
+    def hook(st, batch):
+        if st == _lib.SERVE_FAULT_LAUNCH and batch == 1:
+            calls.append(batch)
+            return len(calls) == 3
+        return False
+
+    srv.set_hook(hook)
+    try:
+        waves = []
+        for w in range(3):
+            tk = [srv.submit(rng, nv=nv, m=m) for nv, m in sizes]
+            waves.append(srv.wait(tk))
+        _ok(srv, waves[0])
+        _failed(waves[1], _lib.ST_FAILED)
+        _ok(srv, waves[2])
+        st = srv.stats()
+        assert len(calls) == 3
+        assert st["failed_launches"] == 1 and st["batches"] == 3
+    finally:
+        srv.close()
+
+
 def test_failure_while_another_batch_is_in_flight(fake):
     rng = np.random.default_rng(7)
     srv = FakeServer(fake, fixed_batch=4, streams=2, latency_us=30000)
