@@ -5,12 +5,13 @@ Tolerances (per instance, per output array, relative to the oracle's
 infinity norm):  a <= 1e-4;  dqfrc, daref, dJ (and dM, dD) <= 1e-3;  active sets
 bit-identical on non-degenerate instances.  An instance is degenerate when a
 row sits on the cone boundary at the oracle's solution, measured on the scale
-that decides its side: an inactive row with
-jar_i < DEG_MARGIN * (sum_k |J_ik a_k| + |aref_i|), or an active row whose
-force |f_i| = D_i |jar_i| < FORCE_MARGIN * max_k |f_k| (stiff active rows
-have |jar| = |f| / D far below |J a| without being near the boundary).  There
-the active set and the adjoint are not defined (the derivative is local to a
-fixed contact set), so only a is compared.
+that decides its side: a row with |jar_i| < DEG_MARGIN * (sum_k |J_ik a_k| +
+|aref_i|), and if it is active also a force |f_i| = D_i |jar_i| <
+FORCE_MARGIN * max_k |f_k| (stiff active rows have |jar| = |f| / D far below
+|J a| without being near the boundary, and a soft row's small force alone
+does not put it there).  There the active set and the adjoint are not
+defined (the derivative is local to a fixed contact set), so only a is
+compared.
 """
 from __future__ import annotations
 
@@ -118,8 +119,8 @@ def compare(w, gpu, ref, idx, check_act=True):
         scale = np.abs(p["J"].astype(np.float64)) @ np.abs(a_ref) + np.abs(p["aref"])
         f = p["D"].astype(np.float64) * np.minimum(jar, 0.0)
         fmax = np.max(np.abs(f)) if m else 0.0
-        near = np.where(jar < 0, np.abs(f) < FORCE_MARGIN * fmax,
-                        jar < DEG_MARGIN * scale) if m else np.zeros(0, bool)
+        near = ((np.abs(jar) < DEG_MARGIN * scale)
+                & ((jar >= 0) | (np.abs(f) < FORCE_MARGIN * fmax))) if m else np.zeros(0, bool)
         degenerate += bool(np.any(near))
         ea = rel(gpu["a"][ov:ov + nv], a_ref)
         worst["a"] = max(worst["a"], ea)
