@@ -780,13 +780,14 @@ struct WarpSolver {
     }
   }
 
-  // Transposed products over the active rows.  From NV = 16 on the lanes
+  // Transposed products over the active rows.  From NV = 8 on the lanes
   // take (column pair, row group): lane l reads columns 2 (l % NP) and
   // 2 (l % NP) + 1 of J with one 8-byte load, for every kTG-th active row
-  // from l / NP on (kTG = 32 / NP groups: 3 at NV = 18, 2 at NV = 32); the
-  // groups' partial sums meet in the lanes of group 0 by shuffles, and lane j
-  // then takes column j from lane j / 2.  Below NV = 16 lane j walks column
-  // j over every active row.
+  // from l / NP on (kTG = 32 / NP groups: 6 at NV = 9, 3 at NV = 18, 2 at
+  // NV = 32); the groups' partial sums meet in the lanes of group 0 by
+  // shuffles, and lane j then takes column j from lane j / 2.  Below NV = 8
+  // (16 groups and their 15 shuffles for a handful of rows) lane j walks
+  // column j over every active row.
   static constexpr int kTG = 32 / G::NP;
 
   // Group 0's lanes gather the partial sums of the other groups (shuffled
@@ -817,7 +818,7 @@ struct WarpSolver {
                                             float& c) {
     const float* Jm = Js();
     const idx_t* idx = Idx();
-    if constexpr (NV >= 16) {
+    if constexpr (NV >= 8) {
       constexpr int RS = G::JS / 2;  // J row stride in float2
       const int gg = lane / G::NP;
       const float2* Jp = reinterpret_cast<const float2*>(Jm) + lane % G::NP;
@@ -919,7 +920,7 @@ struct WarpSolver {
   __device__ __forceinline__ float jt_active_plain(const float* v) {
     const float* Jm = Js();
     const idx_t* idx = Idx();
-    if constexpr (NV >= 16) {
+    if constexpr (NV >= 8) {
       constexpr int RS = G::JS / 2;
       const int gg = lane / G::NP;
       const float2* Jp = reinterpret_cast<const float2*>(Jm) + lane % G::NP;
