@@ -421,7 +421,9 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
                  "p99_ms": float(np.percentile(v, 99) * 1e3)} for k, v in parts.items()}
     nvs = np.array([len(r["qfrc"]) for r in reqs])
     split["by_nv"] = {int(v): {"p50_ms": float(np.percentile(lat[nvs == v], 50) * 1e3),
-                               "p99_ms": float(np.percentile(lat[nvs == v], 99) * 1e3)}
+                               "p99_ms": float(np.percentile(lat[nvs == v], 99) * 1e3),
+                               "queue_p50_ms": float(np.percentile(parts["queue"][nvs == v], 50) * 1e3),
+                               "service_p50_ms": float(np.percentile(parts["service"][nvs == v], 50) * 1e3)}
                       for v in np.unique(nvs)}
     return {"requests": n, "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "latency_split": split,
