@@ -75,3 +75,23 @@ def test_our_arm_line(cuda_device):
     assert "roofline" in d["configs"]["tiny"] and d["configs"]["tiny"]["value"] > 0
     for k in ("sm_mhz", "sm_max_mhz", "reasons"):
         assert k in d["clocks"], k
+
+
+@pytest.mark.gpu
+def test_serve_leg_line(cuda_device):
+    """The serving leg on a short stream: both policies complete every
+    request, and the continuous policy reports its latency split (client lag,
+    queue, service) and its p50 / p99 per nv class."""
+    d = _line(["--steps", "3", "--warmup", "3", "--warmup-seconds", "0", "--no-e2e",
+               "--no-cpu-baseline", "--no-memory", "--no-elliptic", "--no-ncg", "--configs", "",
+               "--serve-requests", "20000", "--serve-sweep", ""], 900)
+    s = d["serve"]
+    assert s["requests"] == 20000
+    for pol in ("continuous", "fixed_1024"):
+        r = s[pol]
+        assert r["ok"] == 20000 and r["solves_per_s"] > 0, pol
+        assert 0 < r["p50_ms"] <= r["p99_ms"], pol
+        split = r["latency_split"]
+        for k in ("client_lag", "queue", "service"):
+            assert split[k]["p50_ms"] <= split[k]["p99_ms"], (pol, k)
+        assert set(split["by_nv"]) == {3, 9, 18, 96} or set(split["by_nv"]) == {"3", "9", "18", "96"}
