@@ -891,10 +891,38 @@ struct WarpSolver {
     lo = __fmaf_rn(d, xl, __fmaf_rn(d, xh, -hi));
   }
 
+  // M products.  For 8 <= NV <= 16 the lanes take (row, column group): lane
+  // l sums row l % NV over the columns k = l / NV (mod kMG) (kMG = 32 / NV
+  // groups: 3 at NV = 9), and the groups' partial sums meet in lane l of
+  // group 0 by shuffles; otherwise lane j walks row j.
+  static constexpr int kMG = (NV >= 8 && NV <= 16) ? 32 / NV : 1;
+  __device__ __forceinline__ void gather_rows(float& x) const {
+    const float o = x;
+#pragma unroll
+    for (int g = 1; g < kMG; ++g) x += __shfl_sync(kFull, o, lane + g * NV);
+  }
+  __device__ __forceinline__ void gather_rows(float& s, float& c) const {
+    const float os = s, oc = c;
+#pragma unroll
+    for (int g = 1; g < kMG; ++g)
+      add_pair(s, c, __shfl_sync(kFull, os, lane + g * NV), __shfl_sync(kFull, oc, lane + g * NV));
+  }
+
   // (s, c) = (M (vh + vl))_j for lane j (compensated).
   __device__ __forceinline__ void m_times(const float* vh, const float* vl, float& s, float& c) {
     s = 0.f;
     c = 0.f;
+    if constexpr (kMG > 1) {
+      const int gg = lane / NV;
+      if (gg < kMG) {
+        const float* Mr = Ms() + (lane - gg * NV) * G::MS;
+#pragma unroll
+        for (int k = gg; k < NV; k += kMG) dot2(s, c, Mr[k], vh[k], vl[k]);
+      }
+      gather_rows(s, c);
+      if (lane >= NV) s = c = 0.f;
+      return;
+    }
     if (lane < NV) {
       const float* Mr = Ms() + lane * G::MS;
 #pragma unroll (kSB)
@@ -984,6 +1012,16 @@ struct WarpSolver {
   }
   __device__ __forceinline__ float m_times_plain(const float* vh) {
     float s = 0.f;
+    if constexpr (kMG > 1) {
+      const int gg = lane / NV;
+      if (gg < kMG) {
+        const float* Mr = Ms() + (lane - gg * NV) * G::MS;
+#pragma unroll
+        for (int k = gg; k < NV; k += kMG) s = __fmaf_rn(Mr[k], vh[k], s);
+      }
+      gather_rows(s);
+      return (lane < NV) ? s : 0.f;
+    }
     if (lane < NV) {
       const float* Mr = Ms() + lane * G::MS;
 #pragma unroll (kSB)
