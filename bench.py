@@ -325,8 +325,10 @@ def _serve_pool(n_requests, rate, seed, pool_per_class=2048):
 
 
 def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 << 30):
-    """Replay the arrivals against a server through the bulk C calls; latency
-    = completion - scheduled arrival (so any lag of the client counts too)."""
+    """Replay the arrivals against a server (cs_serve_replay submits them on
+    schedule from native code; this thread collects through the bulk C
+    calls); latency = completion - scheduled arrival on the server's clock
+    (so any lag of the client counts too)."""
     import ctypes
     from paper_2607_24959_b300 import _lib, serve
     from paper_2607_24959_b300 import workloads as W
@@ -349,26 +351,16 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
     drain = (ctypes.c_uint64 * 8192)()
     while srv.completed(drain):      # the warm-up's completions are not the stream's
         pass
-    old_switch = sys.getswitchinterval()
-    sys.setswitchinterval(1e-4)   # the producer thread must not wait 5 ms for the GIL
     carr = serve.Server.make_requests(reqs)
     tickets = (ctypes.c_uint64 * n)()
+    t0 = srv.clock() + 0.05
     submitted = [0]
-    t0 = time.monotonic() + 0.05
 
     def producer():
-        k = 0
-        while k < n:
-            now = time.monotonic() - t0
-            k1 = int(np.searchsorted(t_arr, now, side="right"))
-            if k1 > k:
-                got = srv.submit_batch(carr, k, k1, tickets)
-                k += got
-                submitted[0] = k
-            else:
-                dt = t_arr[k] - now
-                if dt > 2e-4:
-                    time.sleep(dt - 1e-4)
+        # the arrivals are submitted on schedule from native code
+        # (cs_serve_replay), so the client's own lag does not depend on the
+        # interpreter; this thread releases the interpreter's lock meanwhile
+        submitted[0] = srv.replay(carr, t_arr, t0, tickets)
         if policy == "fixed":
             srv.flush()
 
@@ -407,7 +399,6 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
             srv.close()
             raise RuntimeError(f"serving did not finish: {collected} of {n} collected")
     th.join(timeout=10.0)
-    sys.setswitchinterval(old_switch)
     st = srv.stats()
     srv.close()
     lat = t_done - (t0 + np.asarray(t_arr))
@@ -454,6 +445,8 @@ def run_serve(args):
                             streams=args.serve_streams)
             row[pol] = {k: res[k] for k in ("p50_ms", "p99_ms", "solves_per_s", "ok",
                                             "mean_batch", "max_inflight")}
+            row[pol]["latency_split"] = {k: res["latency_split"][k]
+                                         for k in ("client_lag", "queue", "service")}
         sweep.append(row)
     if sweep:
         out["rate_sweep"] = sweep

@@ -505,6 +505,23 @@ int cs_serve_submit_batch(cs_server* srv, int32_t n, const cs_request* reqs,
 int cs_serve_poll_batch(cs_server* srv, int32_t n, const uint64_t* tickets,
                         cs_result* res, int32_t* done);
 
+/* The server's clock (seconds, steady; the clock of cs_result's t_submit,
+ * t_start and t_done). */
+double cs_serve_clock(void);
+
+/* A load generator for measurements, run in the calling thread: reqs[i]
+ * (host data, copied at submission as by cs_serve_submit) is submitted once
+ * cs_serve_clock() reaches t0 + t_arrival[i] (seconds, ascending), the ones
+ * due together in one bulk call; tickets[i] receives its ticket.  The thread
+ * sleeps while the next arrival is more than 150 us away and yields closer
+ * to it, so the submission lags the schedule by microseconds rather than by
+ * an interpreter's scheduling.  A full queue (CS_EBUSY) is retried; any
+ * other failure ends the replay.  Returns the number queued (n unless a
+ * submission failed), or the first failure's code if none was queued;
+ * CS_EINVAL for NULL arrays with n > 0. */
+int cs_serve_replay(cs_server* srv, int32_t n, const cs_request* reqs,
+                    const double* t_arrival, double t0, uint64_t* tickets);
+
 /* Tickets whose requests completed since the previous call, in completion
  * order (at most max of them, written to tickets); returns their number.
  * A client that holds many outstanding tickets collects exactly these with

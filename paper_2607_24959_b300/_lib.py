@@ -166,6 +166,10 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_uint64)]),
     "cs_serve_poll_batch": (ctypes.c_int, [c_void_p, c_int32, ctypes.POINTER(ctypes.c_uint64),
                                            ctypes.POINTER(CsResult), ctypes.POINTER(c_int32)]),
+    "cs_serve_clock": (ctypes.c_double, []),
+    "cs_serve_replay": (ctypes.c_int, [c_void_p, c_int32, ctypes.POINTER(CsRequest),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_uint64)]),
     "cs_serve_flush": (ctypes.c_int, [c_void_p]),
     "cs_serve_get_stats": (ctypes.c_int, [c_void_p, ctypes.POINTER(CsServeStats)]),
     "cs_serve_destroy": (None, [c_void_p]),

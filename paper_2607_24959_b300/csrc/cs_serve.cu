@@ -151,6 +151,14 @@ int cs_serve_submit_batch(cs_server* S, int32_t n, const cs_request* reqs, uint6
   return S->submit_batch(n, reqs, tickets);
 }
 
+int cs_serve_replay(cs_server* S, int32_t n, const cs_request* reqs, const double* t_arrival,
+                    double t0, uint64_t* tickets) {
+  if (!S) return set_error(CS_EINVAL, "server must not be NULL");
+  return S->replay(n, reqs, t_arrival, t0, tickets);
+}
+
+double cs_serve_clock(void) { return cs_serve::now_s(); }
+
 int cs_serve_poll_batch(cs_server* S, int32_t n, const uint64_t* tickets, cs_result* res,
                         int32_t* done) {
   if (!S) return set_error(CS_EINVAL, "server must not be NULL");

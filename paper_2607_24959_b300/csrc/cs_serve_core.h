@@ -676,6 +676,41 @@ struct Server {
     return n;
   }
 
+  // A load generator in the calling thread: reqs[i] is submitted once the
+  // steady clock reaches t0 + t_arrival[i] (seconds, ascending), the ones
+  // due together in one bulk call.  It sleeps while the next arrival is more
+  // than 150 us away and yields closer to it; a full queue (CS_EBUSY) is
+  // retried, any other failure ends the replay.  Returns the number queued
+  // (n unless a submission failed), or the first failure's code if none was.
+  int replay(int32_t n, const cs_request* reqs, const double* t_arrival, double t0,
+             uint64_t* t) {
+    if (n < 0 || (n > 0 && (!reqs || !t_arrival || !t)))
+      return be.set_error(CS_EINVAL, "requests, arrival times and tickets must not be NULL");
+    int32_t k = 0;
+    while (k < n) {
+      const double now = now_s();
+      int32_t k1 = k;
+      while (k1 < n && t0 + t_arrival[k1] <= now) ++k1;
+      if (k1 > k) {
+        const int got = submit_batch(k1 - k, reqs + k, t + k);
+        if (got == CS_EBUSY) {
+          std::this_thread::yield();
+        } else if (got < 0) {
+          return k > 0 ? k : got;
+        } else {
+          k += got;
+        }
+      } else {
+        const double dt = t0 + t_arrival[k] - now;
+        if (dt > 150e-6)
+          std::this_thread::sleep_for(std::chrono::duration<double>(dt - 100e-6));
+        else
+          std::this_thread::yield();
+      }
+    }
+    return k;
+  }
+
   int poll_batch(int32_t n, const uint64_t* t, cs_result* res, int32_t* done) {
     if (n < 0 || (n > 0 && (!t || !res || !done)))
       return be.set_error(CS_EINVAL, "tickets, results and done must not be NULL");

@@ -110,6 +110,26 @@ class Server:
             _lib.check(rc, "cs_serve_submit_batch")
         return rc
 
+    def clock(self) -> float:
+        """The server's clock in seconds (cs_serve_clock)."""
+        return float(self._lib.cs_serve_clock())
+
+    def replay(self, reqs, t_arrival, t0, tickets) -> int:
+        """Submit reqs (a make_requests array) at t0 + t_arrival[i] on the
+        server's clock from native code (cs_serve_replay; the interpreter's
+        lock is released for the call, so another thread can collect
+        meanwhile); tickets (ctypes uint64 array) receives the tickets.
+        Returns the number queued."""
+        t = np.ascontiguousarray(t_arrival, dtype=np.float64)
+        n = len(t)
+        base = ctypes.cast(reqs, ctypes.POINTER(_lib.CsRequest))
+        tp = t.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        tk = ctypes.cast(tickets, ctypes.POINTER(ctypes.c_uint64))
+        rc = self._lib.cs_serve_replay(self._h, n, base, tp, float(t0), tk)
+        if rc < 0:
+            _lib.check(rc, "cs_serve_replay")
+        return rc
+
     def poll_batch(self, tickets, start, stop, results, done):
         """Poll tickets[start:stop] without copying outputs; results (CsResult
         array) and done (int32 array) are filled at the same indices."""

@@ -113,6 +113,11 @@ int fake_serve_get_stats(void* S, cs_serve_stats* st) { return ((FakeServer*)S)-
 int fake_serve_set_fault_hook(void* S, cs_serve_fault_fn f, void* u) {
   return ((FakeServer*)S)->set_fault_hook(f, u);
 }
+int fake_serve_replay(void* S, int32_t n, const cs_request* reqs, const double* t_arrival,
+                      double t0, uint64_t* t) {
+  return ((FakeServer*)S)->replay(n, reqs, t_arrival, t0, t);
+}
+double fake_serve_clock(void) { return cs_serve::now_s(); }
 void fake_serve_destroy(void* S) {
   ((FakeServer*)S)->destroy();
   delete (FakeServer*)S;

@@ -39,6 +39,10 @@ def fake(tmp_path_factory):
     lib.fake_serve_flush.argtypes = [vp]
     lib.fake_serve_get_stats.argtypes = [vp, ctypes.POINTER(_lib.CsServeStats)]
     lib.fake_serve_set_fault_hook.argtypes = [vp, _lib.SERVE_FAULT_FN, vp]
+    lib.fake_serve_replay.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(_lib.CsRequest),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_uint64)]
+    lib.fake_serve_clock.restype = ctypes.c_double
     lib.fake_serve_destroy.argtypes = [vp]
     lib.fake_serve_destroy.restype = None
     lib.fake_last_error.restype = ctypes.c_char_p
@@ -95,7 +99,7 @@ class FakeServer:
                 if rc == _lib.CS_PENDING:
                     continue
                 assert rc == 0, self.lib.fake_last_error()
-                out[t] = dict(status=res.status, iters=res.iters, **bufs)
+                out[t] = dict(status=res.status, iters=res.iters, t_submit=res.t_submit, **bufs)
             assert time.monotonic() < t_end, "requests did not complete"
             time.sleep(1e-3)
         return out
@@ -238,5 +242,42 @@ def test_hook_removed(fake):
         _failed(srv.wait([srv.submit(rng) for _ in range(2)]), _lib.ST_FAILED)
         srv.set_hook(None)
         _ok(srv, srv.wait([srv.submit(rng) for _ in range(2)]))
+    finally:
+        srv.close()
+
+
+def test_replay_submits_on_schedule(fake):
+    """The native load generator (cs_serve_replay's core): every request is
+    queued no earlier than its scheduled arrival on the server's clock and,
+    on an idle host, shortly after it; all complete."""
+    rng = np.random.default_rng(12)
+    srv = FakeServer(fake, policy="continuous", streams=2, latency_us=100)
+    try:
+        n = 64
+        data = [dict(M=np.eye(6, dtype=np.float32),
+                     J=rng.standard_normal((8, 6)).astype(np.float32),
+                     qfrc=rng.standard_normal(6).astype(np.float32),
+                     aref=rng.standard_normal(8).astype(np.float32),
+                     D=np.full(8, 10.0, np.float32),
+                     g=rng.standard_normal(6).astype(np.float32)) for _ in range(n)]
+        reqs = (_lib.CsRequest * n)()
+        for r, d in zip(reqs, data):
+            r.nv, r.m = 6, 8
+            r.M, r.J, r.qfrc, r.aref, r.D, r.g = (d[k].ctypes.data for k in
+                                                  ("M", "J", "qfrc", "aref", "D", "g"))
+        t_arr = np.cumsum(rng.exponential(2e-4, n))          # about 5 k req/s
+        tickets = (ctypes.c_uint64 * n)()
+        t0 = fake.fake_serve_clock() + 0.01
+        got = fake.fake_serve_replay(srv.h, n, reqs,
+                                     t_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     t0, tickets)
+        assert got == n
+        for t, d in zip(tickets, data):
+            srv.req[t] = d
+        res = srv.wait(list(tickets))
+        _ok(srv, res)
+        lag = np.array([res[t]["t_submit"] for t in tickets]) - (t0 + t_arr)
+        assert np.all(lag >= 0.0), lag.min()
+        assert np.median(lag) < 5e-3, np.median(lag)
     finally:
         srv.close()
