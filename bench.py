@@ -324,7 +324,8 @@ def _serve_pool(n_requests, rate, seed, pool_per_class=2048):
     return t, reqs
 
 
-def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 << 30):
+def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 << 30,
+              clients=1):
     """Replay the arrivals against a server (cs_serve_replay submits them on
     schedule from native code; this thread collects through the bulk C
     calls); latency = completion - scheduled arrival on the server's clock
@@ -351,20 +352,32 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
     drain = (ctypes.c_uint64 * 8192)()
     while srv.completed(drain):      # the warm-up's completions are not the stream's
         pass
-    carr = serve.Server.make_requests(reqs)
-    tickets = (ctypes.c_uint64 * n)()
+    # the stream's tickets follow the warm-up's without a gap, in submission
+    # order (they are global to the server, whichever thread submits)
+    base_ticket = max(int(tk) for tk in wt) + 1
+    subsets = [np.arange(j, n, clients) for j in range(clients)]
+    carrs = [serve.Server.make_requests([reqs[i] for i in sub]) for sub in subsets]
+    tks = [(ctypes.c_uint64 * len(sub))() for sub in subsets]
     t0 = srv.clock() + 0.05
-    submitted = [0]
+    submitted = [0] * clients
 
-    def producer():
+    def producer(j):
         # the arrivals are submitted on schedule from native code
         # (cs_serve_replay), so the client's own lag does not depend on the
-        # interpreter; this thread releases the interpreter's lock meanwhile
-        submitted[0] = srv.replay(carr, t_arr, t0, tickets)
+        # interpreter; the thread releases the interpreter's lock meanwhile.
+        # With several clients each replays every clients-th arrival.
+        submitted[j] = srv.replay(carrs[j], t_arr[subsets[j]], t0, tks[j])
+
+    def producers():
+        ths = [threading.Thread(target=producer, args=(j,), daemon=True) for j in range(clients)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
         if policy == "fixed":
             srv.flush()
 
-    th = threading.Thread(target=producer, daemon=True)
+    th = threading.Thread(target=producers, daemon=True)
     th.start()
     # collect exactly the tickets the server reports as completed (no scan
     # of the outstanding ones under the server's lock)
@@ -387,7 +400,7 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
                 if dtmp[i] != 1:
                     srv.close()
                     raise RuntimeError("serving lost a ticket")
-                idx = int(comp[i]) - int(tickets[0])   # tickets are consecutive
+                idx = int(comp[i]) - base_ticket      # submission position
                 t_done[idx] = rtmp[i].t_done
                 t_sub[idx] = rtmp[i].t_submit
                 t_start[idx] = rtmp[i].t_start
@@ -401,6 +414,12 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
     th.join(timeout=10.0)
     st = srv.stats()
     srv.close()
+    # from submission positions back to the stream's order
+    perm = np.empty(n, np.int64)
+    for sub, tk in zip(subsets, tks):
+        perm[np.frombuffer(tk, dtype=np.uint64).astype(np.int64) - base_ticket] = sub
+    for arr in (t_done, t_sub, t_start, status):
+        arr[perm] = arr.copy()
     lat = t_done - (t0 + np.asarray(t_arr))
     span = t_done.max() - (t0 + t_arr[0])
     # where the latency goes: the client's lag behind the scheduled arrival,
@@ -430,10 +449,13 @@ def run_serve(args):
     a sweep of the arrival rate (the same mix, fewer requests per rate above
     the headline one) to find where each policy stops keeping up."""
     t_arr, reqs = _serve_pool(args.serve_requests, args.serve_rate, 1005)
-    cont = serve_run(t_arr, reqs, "continuous", streams=args.serve_streams)
-    fixed = serve_run(t_arr, reqs, "fixed", fixed_batch=args.serve_fixed_batch)
+    cont = serve_run(t_arr, reqs, "continuous", streams=args.serve_streams,
+                     clients=args.serve_clients)
+    fixed = serve_run(t_arr, reqs, "fixed", fixed_batch=args.serve_fixed_batch,
+                      clients=args.serve_clients)
     out = {"requests": args.serve_requests, "rate_per_s": args.serve_rate,
            "mix": "nv {3,9,18,96} p {.3,.3,.3,.1}, nc U{0..64}, fwd + adjoint each",
+           "client_threads": args.serve_clients,
            "continuous": cont, f"fixed_{args.serve_fixed_batch}": fixed}
     sweep = []
     for rate in [float(r) for r in args.serve_sweep.split(",") if r]:
@@ -442,7 +464,7 @@ def run_serve(args):
         row = {"rate_per_s": rate, "requests": n}
         for pol in ("continuous", "fixed"):
             res = serve_run(t_s, r_s, pol, fixed_batch=args.serve_fixed_batch,
-                            streams=args.serve_streams)
+                            streams=args.serve_streams, clients=args.serve_clients)
             row[pol] = {k: res[k] for k in ("p50_ms", "p99_ms", "solves_per_s", "ok",
                                             "mean_batch", "max_inflight")}
             row[pol]["latency_split"] = {k: res["latency_split"][k]
@@ -1025,6 +1047,8 @@ def main():
     ap.add_argument("--serve-fixed-batch", type=int, default=1024)
     ap.add_argument("--serve-streams", type=int, default=8,
                     help="batches in flight at once for the continuous policy (1..16)")
+    ap.add_argument("--serve-clients", type=int, default=1,
+                    help="client threads replaying the arrivals (each every n-th one)")
     ap.add_argument("--serve-sweep", default="200000,500000,1000000",
                     help="arrival rates (req/s) of the serving sweep; empty to skip")
     args = ap.parse_args()
