@@ -438,7 +438,9 @@ def serve_run(t_arr, reqs, policy, fixed_batch=1024, streams=8, arena_bytes=2 <<
     return {"requests": n, "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "latency_split": split,
             "mean_ms": float(lat.mean() * 1e3), "solves_per_s": n / span,
-            "ok": int(np.sum(status == 0)), "batches": int(st["batches"]),
+            "ok": int(np.sum(status == 0)),
+            "status_counts": {int(k): int(v) for k, v in zip(*np.unique(status, return_counts=True))},
+            "batches": int(st["batches"]),
             "mean_batch": st["batched_requests"] / max(st["batches"], 1),
             "max_inflight": int(st["max_inflight"])}
 
